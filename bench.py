@@ -1,0 +1,333 @@
+#!/usr/bin/env python
+"""Benchmark: HGF multi-label aggregation + WTA on one GB300 (or N independent replicas).
+
+One step = the whole hot path on one synthetic stereo workload already resident in device
+memory: guidance precompute (polynomial guidance, moments, float64 covariance assembly and the
+Prop. 1 inverse) followed by the fused aggregation of every label slice and WTA. The default
+workload is the 450x375 stereo pair with 60 labels, degree-2 monomial guidance (n = 9), r = 9,
+eps = 1e-4, float32 costs. The inputs (40.5 MB of costs) are smaller than L2, so a 256 MiB buffer
+is written between timed steps (outside the timed events) to flush L2.
+
+Metric: Mpixel*labels/s = H * W * L * steps / device time, summed over replicas.
+Prints one JSON line (rank 0). --impl reference times the CPU oracle on a bounded crop instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpixel*labels/s HGF aggregate+WTA (n=9)"
+UNIT = "Mpixel*labels/s"
+WORKLOADS = {
+    "quarter": dict(width=450, height=375, n_labels=60, degree=2, r=9, eps=1e-4, dtype="f32",
+                    seed=2, name="stereo 450x375, L=60, RGB degree-2 monomials (n=9), r=9, "
+                                 "eps=1e-4, float32 costs"),
+    "small": dict(width=64, height=48, n_labels=16, degree=1, r=4, eps=1e-4, dtype="f32", seed=1,
+                  name="stereo 64x48, L=16, RGB (n=3), r=4, eps=1e-4, float32 costs"),
+    "large": dict(width=1400, height=1100, n_labels=256, degree=2, r=9, eps=1e-4, dtype="bf16",
+                  seed=3, name="stereo 1400x1100, L=256, n=9, r=9, eps=1e-4, bf16 costs"),
+}
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+FP64_PEAK_TFLOPS = 1.25                              # nominal GB300 FP64 rate
+
+
+def flops_per_unit(kernel: str, n: int) -> tuple[float, str] | None:
+    """Algorithmic flops per unit (pixel*label for the aggregation kernels, pixel for the
+    inverse) and the unit name."""
+    if kernel == "k_coef":      # n products, 5(n+1) box, 2n cov, 2n^2 mat-vec, 2n offset
+        return 2 * n * n + 10 * n + 5, "px*label"
+    if kernel == "k_apply":     # 5(n+1) box, 2n output, 1 compare
+        return 7 * n + 6, "px*label"
+    if kernel == "k_inverse":   # Prop. 1 recursion + assembly + read-off (float64)
+        rec = sum(3 * k * k + 5 * k + 4 for k in range(n))
+        return rec + 1.5 * n * (n + 1), "px"
+    return None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["fused", "plain", "reference"], default="fused")
+    ap.add_argument("--workload", choices=list(WORKLOADS), default="quarter")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-crop", type=int, nargs=2, default=(225, 188),
+                    help="width height of the centred crop the CPU baseline runs on")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------ CPU oracle arm
+ORACLE_SNIPPET = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+from oracle import hgf_oracle as O
+from paper_1803_00005_gb300 import synth
+w = {w!r}
+case = synth.make_case(w["width"], w["height"], w["n_labels"], w["seed"], w["dtype"])
+cw, ch = {crop!r}
+H, W = w["height"], w["width"]
+y0, x0 = (H - ch) // 2, (W - cw) // 2
+I = case.guidance[:, y0:y0 + ch, x0:x0 + cw]
+P = synth.from_dtype(case.cost[:, y0:y0 + ch, x0:x0 + cw], w["dtype"])
+times = []
+for rep in range({reps}):
+    t = time.perf_counter()
+    q = O.centred_filter(I, P, w["r"], w["eps"], w["degree"])
+    labels = O.wta(q)[0]
+    times.append(time.perf_counter() - t)
+print(json.dumps(dict(times=times, units=cw * ch * P.shape[0])))
+"""
+
+
+def run_oracle(w, crop, reps):
+    """Times the CPU oracle (float64, single thread) on a centred crop with all labels, in a
+    fresh interpreter (no GPU state, BLAS/OpenMP pinned to one thread)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ORACLE_SNIPPET.format(root=ROOT, w=w, crop=tuple(crop), reps=reps)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                         timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def reference_arm(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    crop = (min(150, w["width"]), min(125, w["height"]))
+    res = run_oracle(w, crop, args.warmup + args.steps)
+    t = res["times"][args.warmup:]
+    total = sum(t)
+    value = res["units"] * len(t) / total / 1e6
+    sample = (f"centred {crop[0]}x{crop[1]} crop of the {w['width']}x{w['height']} workload, all "
+              f"{w['n_labels']} labels, prepare + aggregate + WTA per step")
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1e3 * total / len(t), higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                impl="reference",
+                config=dict(workload=w["name"], sample=sample, l2="n/a (CPU)"),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=1, kind="oracle", sample=sample),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["no samples"])
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return dict(sm_mhz=statistics.median(sm) if sm else None,
+                    sm_max_mhz=max(mx) if mx else None, reasons=reasons, samples=len(rows))
+
+
+# ---------------------------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return reference_arm(args, w)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        crop = (min(args.cpu_crop[0], w["width"]), min(args.cpu_crop[1], w["height"]))
+        res = run_oracle(w, crop, 2)            # before any GPU work in this process
+        tot = sum(res["times"])
+        cpu = dict(value=res["units"] * len(res["times"]) / tot / 1e6, unit=UNIT, cores=1,
+                   kind="oracle",
+                   sample=f"centred {crop[0]}x{crop[1]} crop, all {w['n_labels']} labels, "
+                          f"prepare + aggregate + WTA, 2 repetitions ({tot:.1f} s), float64 numpy, "
+                          f"one thread")
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+
+    from paper_1803_00005_gb300 import build, hgf, synth
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+
+    case = synth.make_case(w["width"], w["height"], w["n_labels"], w["seed"], w["dtype"])
+    L, H, W = case.cost.shape
+    n = hgf.hgf_num_channels(3, w["degree"])
+    img = torch.from_numpy(case.guidance).to(dev)
+    if w["dtype"] == "bf16":
+        cost = torch.from_numpy(case.cost.view(np.int16)).to(dev).view(torch.bfloat16)
+    else:
+        cost = torch.from_numpy(case.cost).to(dev)
+    labels = torch.empty((H, W), dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    ctx = hgf.hgf_create(local_rank)
+    params = hgf.make_params(degree=w["degree"], r=w["r"], eps=w["eps"])
+    g = hgf.hgf_prepare(ctx, img, params)
+    agg = hgf.hgf_aggregate_plain if args.impl == "plain" else hgf.hgf_aggregate
+
+    def step():
+        hgf.hgf_guidance_update(ctx, g, img)
+        agg(ctx, g, cost, labels=labels)
+
+    for i in range(args.warmup):
+        flush.fill_(i & 0xff)
+        step()
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local_rank)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = hgf.hgf_launch_count(ctx)
+    hgf.hgf_profile_enable(ctx, True)
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_((i + 7) & 0xff)           # L2 flush, outside the step's events
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    hgf.hgf_profile_enable(ctx, False)
+    launches = hgf.hgf_launch_count(ctx) - launches0
+    prof = hgf.hgf_profile_report(ctx)
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_dev = sum(step_ms) / 1e3
+    t_max = t_dev
+    if world > 1:
+        tt = torch.tensor([t_dev], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    units = H * W * L * args.steps
+    value = world * units / t_max / 1e6
+
+    # roofline of the dominant kernel (largest share of the profiled time)
+    kernels = {k: dict(launches=v["launches"], ms_per_step=v["ms"] / args.steps)
+               for k, v in prof.items()}
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])[0] if prof else None
+    roof = None
+    if dom is not None:
+        fu = flops_per_unit(dom, n)
+        avg_s = prof[dom]["ms"] / prof[dom]["launches"] / 1e3
+        if fu is not None:
+            per_unit, uname = fu
+            launches_per_step = prof[dom]["launches"] / args.steps
+            units_per_launch = (H * W * L if uname == "px*label" else H * W) / launches_per_step
+            achieved = per_unit * units_per_launch / avg_s / 1e12
+            peak = FP64_PEAK_TFLOPS if dom == "k_inverse" else FP32_PEAK_TFLOPS
+            roof = dict(bound="alu", kernel=dom, achieved=achieved, peak=peak, unit="TFLOP/s",
+                        frac=achieved / peak, traffic=None,
+                        model=f"{per_unit:.0f} flops per {uname}",
+                        peak_note=("nominal float64 rate" if dom == "k_inverse" else
+                                   "152 SMs x 128 FP32 lanes x 2 x 2070 MHz"))
+
+    e2e = None
+    if not args.no_e2e:
+        pin_img = torch.from_numpy(case.guidance).pin_memory()
+        raw = case.cost.view(np.int16) if w["dtype"] == "bf16" else case.cost
+        pin_cost = torch.from_numpy(np.ascontiguousarray(raw)).pin_memory()
+        pin_lab = torch.empty((H, W), dtype=torch.int32).pin_memory()
+        hctx = hgf.hgf_create(local_rank)
+        hgf.hgf_filter_host(hctx, pin_img.numpy(), pin_cost.numpy(), w["dtype"], params,
+                            pin_lab.numpy())
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            hgf.hgf_filter_host(hctx, pin_img.numpy(), pin_cost.numpy(), w["dtype"], params,
+                                pin_lab.numpy())
+        te = time.perf_counter() - t0
+        hgf.hgf_destroy(hctx)
+        if world > 1:
+            tt = torch.tensor([te], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = dict(value=world * units / te / 1e6, unit=UNIT,
+                   h2d_bytes_per_step=int(pin_img.numel() * 4 + pin_cost.numel() *
+                                          pin_cost.element_size()),
+                   d2h_bytes_per_step=int(H * W * 4))
+
+    hgf.hgf_guidance_release(g)
+    hgf.hgf_destroy(ctx)
+    if rank == 0:
+        line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
+                    warmup=args.warmup, ms_per_step=1e3 * t_max / args.steps,
+                    higher_is_better=True, scaling="weak", vs_baseline=None,
+                    dtype="f32 (f64 inverse)", data="synthetic",
+                    impl=args.impl,
+                    config=dict(workload=w["name"], parallelism=f"replicas x{world}",
+                                l2="256 MiB buffer written between timed steps",
+                                step="guidance precompute + aggregate + WTA"),
+                    roofline=roof, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches),
+                    clocks=clk, kernels=kernels, wall_s=wall,
+                    step_ms=dict(min=min(step_ms), median=statistics.median(step_ms)))
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,163 @@
+/*
+ * hgf.h - C ABI of libhgf: multichannel guided aggregation of a cost volume with the
+ * Hardware-efficient Guided Filter (HGF, arXiv 1803.00005) followed by winner-takes-all (WTA)
+ * label selection, on one NVIDIA GB300 (sm_103a).
+ *
+ * Problem statement (Sec. 1): a multi-label system records the cost c of label l at pixel (x, y)
+ * in a cost volume V(x, y, l); every label slice is smoothed by a guided filter and each pixel
+ * then takes the label of lowest filtered cost (WTA). The guidance is a polynomial synthesis of
+ * an input image (Sec. 4.2); the per-pixel n x n regularised covariance is inverted once per
+ * guidance with the Sherman-Morrison recursion of Prop. 1 (Sec. 3) and kept resident on the GPU.
+ *
+ * Conventions for every entry point:
+ *   - Images and volumes are planar, row-major, x fastest: an image is C x H x W floats, a cost
+ *     volume is L x H x W elements, label-major (one contiguous H x W slice per label).
+ *   - Pointers documented as "device" must point to memory on the context's device; the caller
+ *     owns them and must keep them valid until the work queued on `stream` has completed.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream). Calls only
+ *     enqueue work; nothing is synchronised unless stated.
+ *   - Every call returns an hgf_status; nothing aborts, traps or throws across this ABI.
+ *     HGF_EINVAL: bad argument (nothing enqueued). HGF_ECUDA: a CUDA call failed; the context
+ *     records it (hgf_last_error) and refuses further work with HGF_ECUDA (sticky).
+ *   - Windows are (2r+1) x (2r+1) boxes clipped at the image border (no padding); means divide
+ *     by the number of in-image pixels N(x, y) (the paper's A(X) = B(X) / B(G0), Eq. HGF_z2).
+ */
+#ifndef HGF_H_
+#define HGF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HGF_OK = 0,
+  HGF_EINVAL = 1,        /* invalid argument */
+  HGF_ENOMEM = 2,        /* device allocation failed, or a request exceeds the memory budget */
+  HGF_ECUDA = 3,         /* CUDA runtime error (sticky per context) */
+  HGF_ETIMEOUT = 4,      /* a bounded wait ran out */
+  HGF_EBUSY = 5,         /* queue full */
+  HGF_EAGAIN = 6,        /* not finished yet */
+  HGF_EUNSUPPORTED = 7   /* valid but not supported (e.g. n > 19) */
+} hgf_status;
+
+typedef enum { HGF_F32 = 0, HGF_BF16 = 1, HGF_F16 = 2, HGF_F64 = 3 } hgf_dtype;
+
+/* Guidance basis (Sec. 4.2). MONOMIAL: every monomial of degree 1..d of the C input channels,
+ * degree-major then lexicographic (R, G, B, RR, RG, RB, GG, GB, BB, RRR, ...), n = C(C+d,d) - 1.
+ * POWERS: the paper's G_{(i-1)d+j} = I_i^j, channel-major, n = C d. */
+typedef enum { HGF_BASIS_MONOMIAL = 0, HGF_BASIS_POWERS = 1 } hgf_basis;
+
+/* How the per-pixel inverse is read off Prop. 1's alpha (Sec. 3). Both run the recursion in the
+ * precision `inv_precision`. W3: lambda^-1 E + S alpha, Eq. HGF_w3 as printed. ALPHA: -lambda alpha,
+ * the same matrix (Prop. 1 gives alpha = -lambda^-1 (lambda E + S)^-1); it skips the n^3/2
+ * multiply-adds of S alpha and the cancellation of lambda^-1 against it. */
+typedef enum { HGF_COMBINE_ALPHA = 0, HGF_COMBINE_W3 = 1 } hgf_combine;
+
+typedef struct {
+  int degree;         /* polynomial degree d >= 1 (Sec. 4.2); n <= 19 */
+  int basis;          /* hgf_basis */
+  int r;              /* window radius r >= 0: (2r+1)^2 box (Sec. 6 uses r = 7) */
+  double eps;         /* regulariser eps > 0 added to the covariance of means (Sec. 5.1, lambda) */
+  int inv_precision;  /* HGF_F64 (default) or HGF_F32: precision of Sigma assembly + recursion */
+  int combine;        /* hgf_combine */
+} hgf_params;
+
+typedef struct hgf_ctx hgf_ctx;
+typedef struct hgf_guidance hgf_guidance;
+
+/* Create a context on CUDA device `device` (makes it current for the calling thread). */
+hgf_status hgf_create(int device, hgf_ctx **out);
+/* Destroy a context: synchronises its device, frees its workspace. Guidance handles created from
+ * it must be released first. NULL is accepted. */
+hgf_status hgf_destroy(hgf_ctx *ctx);
+/* Last error message of this context (empty string if none). Valid until the next call. */
+const char *hgf_last_error(const hgf_ctx *ctx);
+/* Number of guidance channels n for (C, degree, basis); 0 if unsupported. */
+int hgf_num_channels(int C, int degree, int basis);
+
+/* Polynomial guidance synthesis (Sec. 4.2, Eqs. HGF_input_output_polynomial_model[_color]).
+ * img: device, C x H x W float32 (C = 1 or 3). G_out: device, n x H x W float32, channel order
+ * as in hgf_basis. *n_out receives n. */
+hgf_status hgf_make_guidance(hgf_ctx *ctx, const float *img, int C, int H, int W, int degree,
+                             int basis, float *G_out, int *n_out, void *stream);
+
+/* Guidance precompute (Sec. 5.3: guidance-only box filtering is done once per guidance):
+ * polynomial guidance G, means mu = A(G), covariance Sigma = A(G G^T) - mu mu^T plus eps E
+ * (Sec. 5.1) and its inverse by Prop. 1 (Sec. 3), kept resident in a handle the library owns.
+ * img: device, C x H x W float32, may be freed once the call's work has completed (the handle
+ * keeps a copy). The handle's memory is allocated here (HGF_ENOMEM on failure) and freed by
+ * hgf_guidance_release. Bounds: C in {1,3}, 1 <= n <= 19, H, W >= 1, r >= 0, eps > 0. */
+hgf_status hgf_prepare(hgf_ctx *ctx, const float *img, int C, int H, int W,
+                       const hgf_params *params, void *stream, hgf_guidance **out);
+/* Recompute an existing guidance handle from a new image of the same shape and parameters
+ * (same precompute as hgf_prepare, Sec. 5.3), reusing its device memory: no allocation once the
+ * context's prepare workspace has grown to this shape. img: device, C x H x W float32. */
+hgf_status hgf_guidance_update(hgf_ctx *ctx, hgf_guidance *g, const float *img, void *stream);
+/* Release a guidance handle (waits for the device work that uses it). NULL is accepted. */
+hgf_status hgf_guidance_release(hgf_guidance *g);
+/* Shape of a guidance: any pointer may be NULL. */
+hgf_status hgf_guidance_info(const hgf_guidance *g, int *C, int *H, int *W, int *n, int *r,
+                             double *eps);
+/* Copy out the resident inverse for inspection: minv_out (device, n(n+1)/2 x H x W float32,
+ * packed upper triangle row by row: (0,0),(0,1)..(0,n-1),(1,1),..), mu_out (device, n x H x W:
+ * the window means A(G_i)). Either may be NULL. */
+hgf_status hgf_guidance_export(hgf_ctx *ctx, const hgf_guidance *g, float *minv_out,
+                               float *mu_out, void *stream);
+
+/* Fused aggregation + WTA (Sec. 1 pipeline; Eqs. GF_w / HGF_z1): for every label slice p of the
+ * cost volume, pbar = A(p), cov_i = A(G_i p) - mu_i pbar, a = (Sigma + eps E)^-1 cov,
+ * b = pbar - a.mu, q = sum_i A(a_i) G_i + A(b); then labels = argmin_l q_l (lowest l on ties,
+ * NaN counted as +inf) and best = min_l q_l.
+ * cost: device, L x H x W of cost_dtype (HGF_F32, HGF_BF16 or HGF_F16), H, W of the guidance.
+ * filtered: device L x H x W of filtered_dtype (HGF_F32) or NULL; labels: device int32 H x W or
+ * NULL; best: device float32 H x W or NULL. At least one output must be non-NULL.
+ * Uses the context's workspace (grown on demand; HGF_ENOMEM if that fails). */
+hgf_status hgf_aggregate(hgf_ctx *ctx, const hgf_guidance *g, const void *cost, int cost_dtype,
+                         int L, void *filtered, int filtered_dtype, int32_t *labels, float *best,
+                         void *stream);
+
+/* The same computation as hgf_aggregate by the plain form: one kernel per step (products, row
+ * sums, column sums, coefficients, row sums, column sums, output, WTA) with every intermediate
+ * plane in device memory. Comparison baseline for the fused path. Same arguments. */
+hgf_status hgf_aggregate_plain(hgf_ctx *ctx, const hgf_guidance *g, const void *cost,
+                               int cost_dtype, int L, void *filtered, int filtered_dtype,
+                               int32_t *labels, float *best, void *stream);
+
+/* Standalone WTA (Sec. 1) over an already-filtered volume: filtered device L x H x W (HGF_F32),
+ * labels device int32 H x W (or NULL), best device float32 H x W (or NULL). */
+hgf_status hgf_wta(hgf_ctx *ctx, const void *filtered, int dtype, int L, int H, int W,
+                   int32_t *labels, float *best, void *stream);
+
+/* End to end from host memory: copies img (host, C x H x W float32) and cost (host, L x H x W of
+ * cost_dtype) to the device, prepares the guidance, aggregates with WTA and copies labels (host
+ * int32 H x W, may be NULL) and best (host float32 H x W, may be NULL) back; returns after the
+ * results are in host memory. Host buffers may be pageable or pinned (pinned is faster). */
+hgf_status hgf_filter_host(hgf_ctx *ctx, const float *img, int C, int H, int W,
+                           const hgf_params *params, const void *cost, int cost_dtype, int L,
+                           int32_t *labels, float *best, void *stream);
+
+/* Tuning of the fused kernels (0 = automatic): labels per pass of the coefficient and output
+ * kernels, row-band height, labels per chunk of the workspace. Returns HGF_EINVAL for values the
+ * kernels cannot take. */
+typedef struct {
+  int labels_per_pass;
+  int band_rows;
+  int chunk_labels;
+} hgf_tuning;
+hgf_status hgf_set_tuning(hgf_ctx *ctx, const hgf_tuning *t);
+
+/* Instrumentation (no counterpart in the paper). hgf_launch_count: number of kernels this context
+ * has launched since creation. hgf_profile_enable: when on, every kernel launch is bracketed by a
+ * CUDA event pair on its stream. hgf_profile_report: waits for the recorded events, writes
+ * {"kernel": {"launches": n, "ms": total}, ...} as JSON into buf (cap bytes) and clears them. */
+hgf_status hgf_launch_count(hgf_ctx *ctx, unsigned long long *out);
+hgf_status hgf_profile_enable(hgf_ctx *ctx, int enable);
+hgf_status hgf_profile_report(hgf_ctx *ctx, char *buf, size_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HGF_H_ */

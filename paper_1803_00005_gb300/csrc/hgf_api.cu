@@ -1,0 +1,504 @@
+// C ABI of libhgf: argument checks, error mapping, context workspaces and dispatch to the
+// kernels in hgf_prepare.cu, hgf_aggregate.cu and hgf_plain.cu.
+#include "hgf_internal.cuh"
+
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+using namespace hgf;
+
+namespace {
+
+hgf_status set_err(hgf_ctx *ctx, hgf_status st, const char *fmt, ...) {
+  if (!ctx) return st;
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  ctx->err = buf;
+  return st;
+}
+
+hgf_status cuda_fail(hgf_ctx *ctx, cudaError_t e, const char *where) {
+  ctx->sticky.store(HGF_ECUDA);
+  return set_err(ctx, HGF_ECUDA, "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+// Enters an API call on ctx: refuses work after a CUDA failure and makes the device current.
+hgf_status enter(hgf_ctx *ctx) {
+  if (!ctx) return HGF_EINVAL;
+  if (ctx->sticky.load() != HGF_OK)
+    return HGF_ECUDA;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+  return HGF_OK;
+}
+
+bool is_capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) != cudaSuccess) return false;
+  return st != cudaStreamCaptureStatusNone;
+}
+
+// Grows a workspace to at least `bytes` (caller holds ctx->mu). Growing waits for all work on
+// the device (the old buffer may still be in use), so it is refused while `s` is being captured
+// into a graph: make one uncaptured call of the same shape first.
+hgf_status grow(hgf_ctx *ctx, Workspace &w, size_t bytes, cudaStream_t s) {
+  if (w.size >= bytes) return HGF_OK;
+  if (is_capturing(s)) {
+    ctx->err = "workspace must grow to " + std::to_string(bytes) +
+               " bytes; make one uncaptured call first";
+    return HGF_EINVAL;
+  }
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    ctx->sticky.store(HGF_ECUDA);
+    ctx->err = std::string("cudaDeviceSynchronize: ") + cudaGetErrorString(e);
+    return HGF_ECUDA;
+  }
+  if (w.ptr) cudaFree(w.ptr);
+  w.ptr = nullptr;
+  w.size = 0;
+  e = cudaMalloc(&w.ptr, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // allocation failures are not sticky
+    w.ptr = nullptr;
+    ctx->err = "cannot allocate " + std::to_string(bytes) + " bytes of workspace";
+    return HGF_ENOMEM;
+  }
+  w.size = bytes;
+  return HGF_OK;
+}
+
+// CUDA failure with ctx->mu held.
+hgf_status cuda_fail_locked(hgf_ctx *ctx, cudaError_t e, const char *where) {
+  ctx->sticky.store(HGF_ECUDA);
+  ctx->err = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return HGF_ECUDA;
+}
+
+bool valid_dtype_cost(int d) { return d == HGF_F32 || d == HGF_BF16 || d == HGF_F16; }
+
+size_t dtype_size(int d) { return d == HGF_F32 ? 4 : d == HGF_F64 ? 8 : 2; }
+
+hgf_status check_params(hgf_ctx *ctx, int C, int H, int W, const hgf_params *p, int *n_out) {
+  if (!p) return set_err(ctx, HGF_EINVAL, "params is NULL");
+  if (C != 1 && C != 3) return set_err(ctx, HGF_EINVAL, "C must be 1 or 3 (got %d)", C);
+  if (H < 1 || W < 1) return set_err(ctx, HGF_EINVAL, "H and W must be >= 1 (got %d x %d)", H, W);
+  if ((long long)H * W > (1ll << 31) / 64)
+    return set_err(ctx, HGF_EUNSUPPORTED, "image of %d x %d pixels is too large", H, W);
+  if (p->r < 0) return set_err(ctx, HGF_EINVAL, "r must be >= 0 (got %d)", p->r);
+  if (!(p->eps > 0.0)) return set_err(ctx, HGF_EINVAL, "eps must be > 0 (the recursion divides by it)");
+  if (p->degree < 1) return set_err(ctx, HGF_EINVAL, "degree must be >= 1");
+  if (p->basis != HGF_BASIS_MONOMIAL && p->basis != HGF_BASIS_POWERS)
+    return set_err(ctx, HGF_EINVAL, "unknown basis %d", p->basis);
+  if (p->inv_precision != HGF_F64 && p->inv_precision != HGF_F32)
+    return set_err(ctx, HGF_EINVAL, "inv_precision must be HGF_F64 or HGF_F32");
+  if (p->combine != HGF_COMBINE_ALPHA && p->combine != HGF_COMBINE_W3)
+    return set_err(ctx, HGF_EINVAL, "unknown combine %d", p->combine);
+  int n = hgf_num_channels(C, p->degree, p->basis);
+  if (n < 1) return set_err(ctx, HGF_EUNSUPPORTED, "C=%d degree=%d basis=%d gives n > %d", C,
+                            p->degree, p->basis, kMaxChannels);
+  if (!aggregate_supported(n))
+    return set_err(ctx, HGF_EUNSUPPORTED, "n = %d guidance channels are not built", n);
+  *n_out = n;
+  return HGF_OK;
+}
+
+// Windows wider than the image behave like windows covering it: clamp r for the kernels.
+int effective_radius(int r, int H, int W) { return std::min(r, std::max(H, W) - 1); }
+
+hgf_status alloc_guidance(hgf_ctx *ctx, int C, int H, int W, int n, const hgf_params *p,
+                          hgf_guidance **out) {
+  hgf_guidance *g = new (std::nothrow) hgf_guidance;
+  if (!g) return set_err(ctx, HGF_ENOMEM, "host allocation failed");
+  g->ctx = ctx;
+  g->C = C;
+  g->H = H;
+  g->W = W;
+  g->n = n;
+  g->degree = p->degree;
+  g->basis = p->basis;
+  g->r = effective_radius(p->r, H, W);
+  g->eps = p->eps;
+  g->inv_precision = p->inv_precision;
+  g->combine = p->combine;
+  const size_t HW = (size_t)H * W;
+  const size_t floats = HW * ((size_t)n + packed_size(n) + n) + 64;
+  float *base = nullptr;
+  cudaError_t e = cudaMalloc(&base, floats * sizeof(float));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete g;
+    return set_err(ctx, HGF_ENOMEM, "cannot allocate %zu bytes for the guidance",
+                   floats * sizeof(float));
+  }
+  g->G = base;
+  g->minv = g->G + (size_t)n * HW;
+  g->mu = g->minv + (size_t)packed_size(n) * HW;
+  g->shift = g->mu + (size_t)n * HW;
+  *out = g;
+  return HGF_OK;
+}
+
+bool same_shape(const hgf_guidance *g, int C, int H, int W, const hgf_params *p) {
+  return g && g->C == C && g->H == H && g->W == W && g->degree == p->degree &&
+         g->basis == p->basis && g->r == effective_radius(p->r, H, W) && g->eps == p->eps &&
+         g->inv_precision == p->inv_precision && g->combine == p->combine;
+}
+
+hgf_status prepare_locked(hgf_ctx *ctx, hgf_guidance *g, const float *img, cudaStream_t s) {
+  hgf_status st = grow(ctx, ctx->ws_prepare, prepare_workspace_bytes(g->n, g->H, g->W), s);
+  if (st != HGF_OK) return st;
+  cudaError_t e = launch_prepare(g, img, ctx->ws_prepare.ptr, ctx->ws_prepare.size, s,
+                                 &ctx->prof);
+  if (e != cudaSuccess) return cuda_fail_locked(ctx, e, "hgf_prepare");
+  return HGF_OK;
+}
+
+hgf_status check_outputs(hgf_ctx *ctx, const hgf_guidance *g, const void *cost, int cost_dtype,
+                         int L, const void *filtered, int filtered_dtype, const void *labels,
+                         const void *best) {
+  if (!g) return set_err(ctx, HGF_EINVAL, "guidance is NULL");
+  if (g->ctx != ctx) return set_err(ctx, HGF_EINVAL, "guidance belongs to another context");
+  if (!cost) return set_err(ctx, HGF_EINVAL, "cost is NULL");
+  if (!valid_dtype_cost(cost_dtype))
+    return set_err(ctx, HGF_EINVAL, "cost dtype must be HGF_F32, HGF_BF16 or HGF_F16");
+  if (L < 1) return set_err(ctx, HGF_EINVAL, "L must be >= 1 (got %d)", L);
+  if ((long long)L * g->H * g->W > (1ll << 40))
+    return set_err(ctx, HGF_EUNSUPPORTED, "cost volume too large");
+  if (!filtered && !labels && !best) return set_err(ctx, HGF_EINVAL, "no output requested");
+  if (filtered && filtered_dtype != HGF_F32)
+    return set_err(ctx, HGF_EINVAL, "filtered dtype must be HGF_F32");
+  return HGF_OK;
+}
+
+hgf_status aggregate_locked(hgf_ctx *ctx, const hgf_guidance *g, const void *cost,
+                            int cost_dtype, int L, void *filtered, int32_t *labels, float *best,
+                            cudaStream_t s) {
+  if (2 * g->r + 1 > kStripThreads) {
+    ctx->err = "fused path needs 2r+1 < " + std::to_string(kStripThreads);
+    return HGF_EUNSUPPORTED;
+  }
+  AggregatePlan plan = plan_aggregate(g, L, ctx->tuning, ctx->num_sms);
+  if (ctx->tuning.labels_per_pass > 0) plan.K = ctx->tuning.labels_per_pass;
+  hgf_status st = grow(ctx, ctx->ws_coef, aggregate_coef_bytes(g, plan), s);
+  if (st == HGF_OK)
+    st = grow(ctx, ctx->ws_keys, (size_t)g->H * g->W * sizeof(unsigned long long), s);
+  if (st != HGF_OK) return st;
+  cudaError_t e = launch_aggregate(g, cost, cost_dtype, L, (float *)filtered, labels, best,
+                                   (float *)ctx->ws_coef.ptr,
+                                   (unsigned long long *)ctx->ws_keys.ptr, plan, s, &ctx->prof);
+  if (e != cudaSuccess) return cuda_fail_locked(ctx, e, "hgf_aggregate");
+  return HGF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hgf_num_channels(int C, int degree, int basis) {
+  BasisTable t;
+  if (!make_basis_table(C, degree, basis, &t)) return 0;
+  return t.n;
+}
+
+hgf_status hgf_create(int device, hgf_ctx **out) {
+  if (!out) return HGF_EINVAL;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return HGF_EINVAL;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    return HGF_ECUDA;
+  }
+  hgf_ctx *ctx = new (std::nothrow) hgf_ctx;
+  if (!ctx) return HGF_ENOMEM;
+  ctx->device = device;
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  *out = ctx;
+  return HGF_OK;
+}
+
+hgf_status hgf_destroy(hgf_ctx *ctx) {
+  if (!ctx) return HGF_OK;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->host_guidance) {
+    cudaFree(ctx->host_guidance->G);
+    delete ctx->host_guidance;
+  }
+  for (auto &rec : ctx->prof.recs) {
+    cudaEventDestroy(rec.a);
+    cudaEventDestroy(rec.b);
+  }
+  for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
+  for (Workspace *w : {&ctx->ws_prepare, &ctx->ws_coef, &ctx->ws_keys, &ctx->ws_plain,
+                       &ctx->ws_io})
+    if (w->ptr) cudaFree(w->ptr);
+  delete ctx;
+  return HGF_OK;
+}
+
+const char *hgf_last_error(const hgf_ctx *ctx) {
+  if (!ctx) return "context is NULL";
+  return ctx->err.c_str();
+}
+
+hgf_status hgf_make_guidance(hgf_ctx *ctx, const float *img, int C, int H, int W, int degree,
+                             int basis, float *G_out, int *n_out, void *stream) {
+  hgf_status st = enter(ctx);
+  if (st != HGF_OK) return st;
+  if (!img || !G_out) return set_err(ctx, HGF_EINVAL, "img and G_out must be non-NULL");
+  if (H < 1 || W < 1 || (C != 1 && C != 3)) return set_err(ctx, HGF_EINVAL, "bad image shape");
+  BasisTable bt;
+  if (!make_basis_table(C, degree, basis, &bt))
+    return set_err(ctx, HGF_EUNSUPPORTED, "unsupported degree/basis");
+  if (n_out) *n_out = bt.n;
+  cudaError_t e = launch_make_guidance(img, C, H, W, bt, G_out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "hgf_make_guidance");
+  return HGF_OK;
+}
+
+hgf_status hgf_prepare(hgf_ctx *ctx, const float *img, int C, int H, int W,
+                       const hgf_params *params, void *stream, hgf_guidance **out) {
+  hgf_status st = enter(ctx);
+  if (st != HGF_OK) return st;
+  if (!out) return set_err(ctx, HGF_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!img) return set_err(ctx, HGF_EINVAL, "img is NULL");
+  int n = 0;
+  st = check_params(ctx, C, H, W, params, &n);
+  if (st != HGF_OK) return st;
+  hgf_guidance *g = nullptr;
+  st = alloc_guidance(ctx, C, H, W, n, params, &g);
+  if (st != HGF_OK) return st;
+  {
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    st = prepare_locked(ctx, g, img, (cudaStream_t)stream);
+  }
+  if (st != HGF_OK) {
+    cudaFree(g->G);
+    delete g;
+    return st;
+  }
+  *out = g;
+  return HGF_OK;
+}
+
+hgf_status hgf_guidance_release(hgf_guidance *g) {
+  if (!g) return HGF_OK;
+  cudaSetDevice(g->ctx->device);
+  cudaFree(g->G);
+  delete g;
+  return HGF_OK;
+}
+
+hgf_status hgf_guidance_info(const hgf_guidance *g, int *C, int *H, int *W, int *n, int *r,
+                             double *eps) {
+  if (!g) return HGF_EINVAL;
+  if (C) *C = g->C;
+  if (H) *H = g->H;
+  if (W) *W = g->W;
+  if (n) *n = g->n;
+  if (r) *r = g->r;
+  if (eps) *eps = g->eps;
+  return HGF_OK;
+}
+
+hgf_status hgf_guidance_export(hgf_ctx *ctx, const hgf_guidance *g, float *minv_out,
+                               float *mu_out, void *stream) {
+  hgf_status st = enter(ctx);
+  if (st != HGF_OK) return st;
+  if (!g || g->ctx != ctx) return set_err(ctx, HGF_EINVAL, "bad guidance handle");
+  cudaError_t e = launch_export(g, minv_out, mu_out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "hgf_guidance_export");
+  return HGF_OK;
+}
+
+hgf_status hgf_set_tuning(hgf_ctx *ctx, const hgf_tuning *t) {
+  if (!ctx || !t) return HGF_EINVAL;
+  if (t->labels_per_pass != 0 && t->labels_per_pass != 1 && t->labels_per_pass != 2 &&
+      t->labels_per_pass != 4)
+    return set_err(ctx, HGF_EINVAL, "labels_per_pass must be 0, 1, 2 or 4");
+  if (t->band_rows < 0 || t->chunk_labels < 0)
+    return set_err(ctx, HGF_EINVAL, "band_rows and chunk_labels must be >= 0");
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  ctx->tuning = *t;
+  return HGF_OK;
+}
+
+hgf_status hgf_aggregate(hgf_ctx *ctx, const hgf_guidance *g, const void *cost, int cost_dtype,
+                         int L, void *filtered, int filtered_dtype, int32_t *labels, float *best,
+                         void *stream) {
+  hgf_status st = enter(ctx);
+  if (st != HGF_OK) return st;
+  st = check_outputs(ctx, g, cost, cost_dtype, L, filtered, filtered_dtype, labels, best);
+  if (st != HGF_OK) return st;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  return aggregate_locked(ctx, g, cost, cost_dtype, L, filtered, labels, best,
+                          (cudaStream_t)stream);
+}
+
+hgf_status hgf_aggregate_plain(hgf_ctx *ctx, const hgf_guidance *g, const void *cost,
+                               int cost_dtype, int L, void *filtered, int filtered_dtype,
+                               int32_t *labels, float *best, void *stream) {
+  hgf_status st = enter(ctx);
+  if (st != HGF_OK) return st;
+  st = check_outputs(ctx, g, cost, cost_dtype, L, filtered, filtered_dtype, labels, best);
+  if (st != HGF_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  int chunk = 1;
+  size_t need = plain_workspace_bytes(g, L, &chunk);
+  const size_t qbytes = filtered ? 0 : (size_t)L * g->H * g->W * sizeof(float);
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  st = grow(ctx, ctx->ws_plain, need + qbytes, s);
+  if (st != HGF_OK) return st;
+  float *q = filtered ? (float *)filtered : (float *)((char *)ctx->ws_plain.ptr + need);
+  cudaError_t e = launch_aggregate_plain(g, cost, cost_dtype, L, q, labels, best,
+                                         ctx->ws_plain.ptr, chunk, s, &ctx->prof);
+  if (e != cudaSuccess) return cuda_fail_locked(ctx, e, "hgf_aggregate_plain");
+  return HGF_OK;
+}
+
+hgf_status hgf_wta(hgf_ctx *ctx, const void *filtered, int dtype, int L, int H, int W,
+                   int32_t *labels, float *best, void *stream) {
+  hgf_status st = enter(ctx);
+  if (st != HGF_OK) return st;
+  if (!filtered || (!labels && !best)) return set_err(ctx, HGF_EINVAL, "NULL argument");
+  if (dtype != HGF_F32) return set_err(ctx, HGF_EINVAL, "hgf_wta takes HGF_F32 volumes");
+  if (L < 1 || H < 1 || W < 1) return set_err(ctx, HGF_EINVAL, "bad shape");
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  cudaError_t e = launch_wta((const float *)filtered, L, H, W, labels, best,
+                             (cudaStream_t)stream, &ctx->prof);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "hgf_wta");
+  return HGF_OK;
+}
+
+hgf_status hgf_filter_host(hgf_ctx *ctx, const float *img, int C, int H, int W,
+                           const hgf_params *params, const void *cost, int cost_dtype, int L,
+                           int32_t *labels, float *best, void *stream) {
+  hgf_status st = enter(ctx);
+  if (st != HGF_OK) return st;
+  if (!img || !cost || (!labels && !best)) return set_err(ctx, HGF_EINVAL, "NULL argument");
+  if (!valid_dtype_cost(cost_dtype)) return set_err(ctx, HGF_EINVAL, "bad cost dtype");
+  if (L < 1) return set_err(ctx, HGF_EINVAL, "L must be >= 1");
+  int n = 0;
+  st = check_params(ctx, C, H, W, params, &n);
+  if (st != HGF_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t HW = (size_t)H * W;
+  const size_t img_b = ((size_t)C * HW * 4 + 255) / 256 * 256;
+  const size_t cost_b = ((size_t)L * HW * dtype_size(cost_dtype) + 255) / 256 * 256;
+  const size_t out_b = (HW * 4 + 255) / 256 * 256;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  st = grow(ctx, ctx->ws_io, img_b + cost_b + 2 * out_b, s);
+  if (st != HGF_OK) return st;
+  char *base = (char *)ctx->ws_io.ptr;
+  float *img_d = (float *)base;
+  void *cost_d = base + img_b;
+  int32_t *labels_d = (int32_t *)(base + img_b + cost_b);
+  float *best_d = (float *)(base + img_b + cost_b + out_b);
+  cudaError_t e = cudaMemcpyAsync(img_d, img, (size_t)C * HW * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(cost_d, cost, (size_t)L * HW * dtype_size(cost_dtype),
+                        cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail_locked(ctx, e, "hgf_filter_host upload");
+  if (!same_shape(ctx->host_guidance, C, H, W, params)) {
+    if (ctx->host_guidance) {
+      cudaStreamSynchronize(s);
+      cudaFree(ctx->host_guidance->G);
+      delete ctx->host_guidance;
+      ctx->host_guidance = nullptr;
+    }
+    hgf_guidance *g = nullptr;
+    st = alloc_guidance(ctx, C, H, W, n, params, &g);
+    if (st != HGF_OK) return st;
+    ctx->host_guidance = g;
+  }
+  st = prepare_locked(ctx, ctx->host_guidance, img_d, s);
+  if (st != HGF_OK) return st;
+  st = aggregate_locked(ctx, ctx->host_guidance, cost_d, cost_dtype, L, nullptr,
+                        labels ? labels_d : nullptr, best ? best_d : nullptr, s);
+  if (st != HGF_OK) return st;
+  if (labels) e = cudaMemcpyAsync(labels, labels_d, HW * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && best) e = cudaMemcpyAsync(best, best_d, HW * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail_locked(ctx, e, "hgf_filter_host download");
+  return HGF_OK;
+}
+
+
+hgf_status hgf_guidance_update(hgf_ctx *ctx, hgf_guidance *g, const float *img, void *stream) {
+  hgf_status st = enter(ctx);
+  if (st != HGF_OK) return st;
+  if (!g || g->ctx != ctx) return set_err(ctx, HGF_EINVAL, "bad guidance handle");
+  if (!img) return set_err(ctx, HGF_EINVAL, "img is NULL");
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  return prepare_locked(ctx, g, img, (cudaStream_t)stream);
+}
+
+hgf_status hgf_profile_enable(hgf_ctx *ctx, int enable) {
+  if (!ctx) return HGF_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  ctx->prof.enabled = enable != 0;
+  return HGF_OK;
+}
+
+hgf_status hgf_launch_count(hgf_ctx *ctx, unsigned long long *out) {
+  if (!ctx || !out) return HGF_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  *out = ctx->prof.launches;
+  return HGF_OK;
+}
+
+hgf_status hgf_profile_report(hgf_ctx *ctx, char *buf, size_t cap) {
+  hgf_status st = enter(ctx);
+  if (st != HGF_OK) return st;
+  if (!buf || cap == 0) return set_err(ctx, HGF_EINVAL, "NULL buffer");
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  struct Acc {
+    std::string name;
+    int launches;
+    double ms;
+  };
+  std::vector<Acc> acc;
+  for (auto &rec : ctx->prof.recs) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventSynchronize(rec.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, rec.a, rec.b);
+    if (e != cudaSuccess) return cuda_fail_locked(ctx, e, "hgf_profile_report");
+    auto it = std::find_if(acc.begin(), acc.end(), [&](const Acc &a) { return a.name == rec.name; });
+    if (it == acc.end()) {
+      acc.push_back({rec.name, 1, (double)ms});
+    } else {
+      it->launches += 1;
+      it->ms += ms;
+    }
+    ctx->prof.pool.push_back(rec.a);
+    ctx->prof.pool.push_back(rec.b);
+  }
+  ctx->prof.recs.clear();
+  std::string js = "{";
+  for (size_t i = 0; i < acc.size(); ++i) {
+    char item[160];
+    snprintf(item, sizeof item, "%s\"%s\": {\"launches\": %d, \"ms\": %.6f}", i ? ", " : "",
+             acc[i].name.c_str(), acc[i].launches, acc[i].ms);
+    js += item;
+  }
+  js += "}";
+  if (js.size() + 1 > cap) return set_err(ctx, HGF_EINVAL, "buffer too small (%zu)", js.size() + 1);
+  memcpy(buf, js.c_str(), js.size() + 1);
+  return HGF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,184 @@
+// Internal declarations of libhgf (CUDA side). Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/hgf.h"
+
+namespace hgf {
+
+constexpr int kMaxChannels = 19;        // n <= 19 (degree-3 monomials of RGB)
+constexpr int kMaxMonomialDegree = 9;   // gray powers up to I^9 (Table 3 shapes)
+constexpr int kStripThreads = 128;      // threads per CTA of the strip kernels
+
+// Channel multiset table: G_i = prod over chan[i][0..deg[i]-1] of I_chan.
+struct BasisTable {
+  int n;
+  int deg[kMaxChannels];
+  int chan[kMaxChannels][kMaxMonomialDegree];
+};
+
+bool make_basis_table(int C, int degree, int basis, BasisTable *t);
+
+inline int packed_size(int n) { return n * (n + 1) / 2; }
+
+// Packed upper-triangle index of (i, j), i <= j, row by row.
+__host__ __device__ constexpr int tri_index(int n, int i, int j) {
+  return i * n - (i * (i - 1)) / 2 + (j - i);
+}
+
+// Number of in-image samples of the clipped window along one axis.
+__device__ __forceinline__ int clipped_count(int x, int r, int W) {
+  int lo = x - r < 0 ? 0 : x - r;
+  int hi = x + r > W - 1 ? W - 1 : x + r;
+  return hi - lo + 1;
+}
+
+// Cost element loads (storage dtype -> float32).
+__device__ __forceinline__ float load_cost(const float *p, size_t i) { return __ldg(p + i); }
+__device__ __forceinline__ float load_cost(const __nv_bfloat16 *p, size_t i) {
+  return __bfloat162float(p[i]);
+}
+__device__ __forceinline__ float load_cost(const __half *p, size_t i) { return __half2float(p[i]); }
+
+// WTA key: orderable float bits in the high word, label in the low word, so that an unsigned
+// 64-bit minimum picks the lowest cost and, among equal costs, the lowest label. NaN is counted as
+// +inf and -0 as +0 so that equal values compare equal.
+__device__ __forceinline__ unsigned long long wta_key(float q, int label) {
+  if (q != q) q = __int_as_float(0x7f800000);
+  q = q + 0.0f;
+  unsigned int u = __float_as_uint(q);
+  u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+  return ((unsigned long long)u << 32) | (unsigned int)label;
+}
+__device__ __forceinline__ float wta_key_value(unsigned long long key) {
+  unsigned int o = (unsigned int)(key >> 32);
+  unsigned int u = (o & 0x80000000u) ? (o & 0x7fffffffu) : ~o;
+  return __uint_as_float(u);
+}
+
+// ------------------------------------------------------------------------------------------
+// Host-side state
+// ------------------------------------------------------------------------------------------
+struct Workspace {
+  void *ptr = nullptr;
+  size_t size = 0;
+};
+
+// Per-context kernel instrumentation: a launch counter (always on) and, when enabled, a CUDA
+// event pair recorded on the launching stream around every kernel launch.
+struct Profiler {
+  bool enabled = false;
+  unsigned long long launches = 0;
+  struct Rec {
+    const char *name;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get() {
+    cudaEvent_t e = nullptr;
+    if (!pool.empty()) {
+      e = pool.back();
+      pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      e = nullptr;
+    }
+    return e;
+  }
+};
+
+// Brackets one kernel launch: counts it and, if profiling is on, records events around it.
+class LaunchScope {
+ public:
+  LaunchScope(Profiler *p, const char *name, cudaStream_t s) : p_(p), name_(name), s_(s) {
+    if (!p_) return;
+    ++p_->launches;
+    if (p_->enabled) {
+      a_ = p_->get();
+      if (a_) cudaEventRecord(a_, s_);
+    }
+  }
+  ~LaunchScope() {
+    if (!p_ || !p_->enabled || !a_) return;
+    cudaEvent_t b = p_->get();
+    if (!b) return;
+    cudaEventRecord(b, s_);
+    p_->recs.push_back({name_, a_, b});
+  }
+
+ private:
+  Profiler *p_;
+  const char *name_;
+  cudaStream_t s_;
+  cudaEvent_t a_ = nullptr;
+};
+
+}  // namespace hgf
+
+struct hgf_ctx {
+  int device = 0;
+  std::atomic<int> sticky{HGF_OK};
+  std::string err;
+  std::recursive_mutex mu;                // guards the workspaces and err
+  hgf::Workspace ws_prepare;     // moment row sums + reduction partials
+  hgf::Workspace ws_coef;        // per-chunk coefficient planes (fused path)
+  hgf::Workspace ws_keys;        // per-pixel WTA keys
+  hgf::Workspace ws_plain;       // plain-form intermediates
+  hgf::Workspace ws_io;          // device copies for hgf_filter_host
+  hgf_guidance *host_guidance = nullptr;  // reused by hgf_filter_host
+  hgf_tuning tuning{0, 0, 0};
+  int num_sms = 0;
+  hgf::Profiler prof;
+};
+
+struct hgf_guidance {
+  hgf_ctx *ctx = nullptr;
+  int C = 0, H = 0, W = 0, n = 0, degree = 0, basis = 0, r = 0;
+  double eps = 0.0;
+  int inv_precision = HGF_F64, combine = HGF_COMBINE_ALPHA;
+  float *G = nullptr;      // n x H x W, shifted guidance G_i - c_i
+  float *minv = nullptr;   // n(n+1)/2 x H x W, packed (Sigma + eps E)^-1
+  float *mu = nullptr;     // n x H x W, shifted means A(G_i) - c_i
+  float *shift = nullptr;  // n, device: c_i (image mean of G_i)
+};
+
+namespace hgf {
+
+// Kernel launchers (each returns cudaGetLastError() of its launches).
+cudaError_t launch_make_guidance(const float *img, int C, int H, int W, const BasisTable &bt,
+                                 float *G, cudaStream_t s);
+cudaError_t launch_prepare(hgf_guidance *g, const float *img, void *ws, size_t ws_size,
+                           cudaStream_t s, Profiler *prof);
+size_t prepare_workspace_bytes(int n, int H, int W);
+cudaError_t launch_export(const hgf_guidance *g, float *minv_out, float *mu_out, cudaStream_t s);
+
+struct AggregatePlan {
+  int K;            // labels per pass
+  int band_rows;    // coefficient/output rows per CTA band
+  int chunk;        // labels per workspace chunk
+};
+AggregatePlan plan_aggregate(const hgf_guidance *g, int L, const hgf_tuning &t, int num_sms);
+size_t aggregate_coef_bytes(const hgf_guidance *g, const AggregatePlan &p);
+cudaError_t launch_aggregate(const hgf_guidance *g, const void *cost, int cost_dtype, int L,
+                             float *filtered, int32_t *labels, float *best, float *coef_ws,
+                             unsigned long long *keys, const AggregatePlan &p, cudaStream_t s,
+                             Profiler *prof);
+size_t plain_workspace_bytes(const hgf_guidance *g, int L, int *chunk_out);
+cudaError_t launch_aggregate_plain(const hgf_guidance *g, const void *cost, int cost_dtype,
+                                   int L, float *filtered, int32_t *labels, float *best,
+                                   void *ws, int chunk, cudaStream_t s, Profiler *prof);
+cudaError_t launch_wta(const float *filtered, int L, int H, int W, int32_t *labels, float *best,
+                       cudaStream_t s, Profiler *prof);
+bool aggregate_supported(int n);
+
+}  // namespace hgf

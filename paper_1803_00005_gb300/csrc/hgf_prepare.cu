@@ -1,0 +1,333 @@
+// Guidance precompute: polynomial guidance (Sec. 4.2), window moments (Prop. 2: Gram entries are
+// box sums), covariance assembly (Sec. 5.1) and the per-pixel inverse by the Sherman-Morrison
+// recursion of Prop. 1 (Sec. 3). Runs once per guidance; the result stays resident.
+//
+// Numerics: every guidance channel is shifted by its image mean c_i before moments are formed.
+// The centred form is exactly invariant to G_i -> G_i - c_i (Sigma, cov and q do not change), and
+// the shift shrinks the cancellation in A(G_i G_j) - mu_i mu_j. Window sums are float32 direct
+// sums of 2r+1 terms per axis; the assembly Sigma = A(GG^T) - mu mu^T and the recursion run in the
+// precision chosen by hgf_params.inv_precision (float64 by default).
+#include "hgf_internal.cuh"
+
+#include <algorithm>
+
+namespace hgf {
+
+bool make_basis_table(int C, int degree, int basis, BasisTable *t) {
+  if (C < 1 || C > 3 || degree < 1) return false;
+  int n = 0;
+  if (basis == HGF_BASIS_POWERS || C == 1) {
+    if (degree > kMaxMonomialDegree) return false;
+    for (int c = 0; c < C; ++c)
+      for (int j = 1; j <= degree; ++j) {
+        if (n >= kMaxChannels) return false;
+        t->deg[n] = j;
+        for (int k = 0; k < j; ++k) t->chan[n][k] = c;
+        ++n;
+      }
+  } else if (basis == HGF_BASIS_MONOMIAL) {
+    if (degree > 3) return false;
+    // degree-major, then lexicographic multisets c0 <= c1 <= ... (combinations with replacement)
+    for (int d = 1; d <= degree; ++d) {
+      int idx[3] = {0, 0, 0};
+      while (true) {
+        if (n >= kMaxChannels) return false;
+        t->deg[n] = d;
+        for (int k = 0; k < d; ++k) t->chan[n][k] = idx[k];
+        ++n;
+        int k = d - 1;
+        while (k >= 0 && idx[k] == C - 1) --k;
+        if (k < 0) break;
+        ++idx[k];
+        for (int m = k + 1; m < d; ++m) idx[m] = idx[k];
+      }
+    }
+  } else {
+    return false;
+  }
+  t->n = n;
+  return true;
+}
+
+// ---------------------------------------------------------------------------- guidance synthesis
+__global__ void k_make_guidance(const float *__restrict__ img, int C, int HW, BasisTable bt,
+                                float *__restrict__ G) {
+  size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (p >= (size_t)HW) return;
+  float x[3];
+  for (int c = 0; c < C; ++c) x[c] = img[(size_t)c * HW + p];
+  for (int i = 0; i < bt.n; ++i) {
+    float v = x[bt.chan[i][0]];
+    for (int k = 1; k < bt.deg[i]; ++k) v *= x[bt.chan[i][k]];
+    G[(size_t)i * HW + p] = v;
+  }
+}
+
+cudaError_t launch_make_guidance(const float *img, int C, int H, int W, const BasisTable &bt,
+                                 float *G, cudaStream_t s) {
+  int HW = H * W;
+  k_make_guidance<<<(HW + 255) / 256, 256, 0, s>>>(img, C, HW, bt, G);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- per-channel mean (deterministic)
+constexpr int kMeanBlocks = 160;
+constexpr int kMeanThreads = 256;
+
+// partial[b * n + i] = sum of G_i over the pixels of block b's fixed range (float64, fixed order)
+__global__ void k_mean_partial(const float *__restrict__ G, int n, int HW,
+                               double *__restrict__ partial) {
+  __shared__ double red[kMeanThreads];
+  int per = (HW + gridDim.x - 1) / gridDim.x;
+  int p0 = blockIdx.x * per, p1 = min(HW, p0 + per);
+  for (int i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) s += G[(size_t)i * HW + p];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x * n + i] = red[0];
+    __syncthreads();
+  }
+}
+
+__global__ void k_mean_final(const double *__restrict__ partial, int nblk, int n, int HW,
+                             float *__restrict__ shift) {
+  int i = threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += partial[b * n + i];
+  shift[i] = (float)(s / HW);
+}
+
+__global__ void k_apply_shift(float *__restrict__ G, const float *__restrict__ shift, int n,
+                              int HW) {
+  size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (p >= (size_t)HW) return;
+  for (int i = 0; i < n; ++i) G[(size_t)i * HW + p] -= shift[i];
+}
+
+// ------------------------------------------------------------------------- moment row sums
+// Moment channel m < n is G_m; m >= n enumerates the pairs (i, j), i <= j, of the packed upper
+// triangle. rows[m][y][x] = sum over the clipped horizontal window of the channel's values.
+__global__ void k_moment_rows(const float *__restrict__ G, int n, int H, int W, int r,
+                              float *__restrict__ rows) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y;
+  int m = blockIdx.z;
+  if (x >= W) return;
+  size_t HW = (size_t)H * W;
+  int i, j;
+  if (m < n) {
+    i = m;
+    j = -1;
+  } else {
+    int e = m - n;  // packed index -> (i, j)
+    i = 0;
+    while (e >= n - i) {
+      e -= n - i;
+      ++i;
+    }
+    j = i + e;
+  }
+  const float *gi = G + (size_t)i * HW + (size_t)y * W;
+  const float *gj = j >= 0 ? G + (size_t)j * HW + (size_t)y * W : nullptr;
+  int lo = max(0, x - r), hi = min(W - 1, x + r);
+  float s = 0.f;
+  if (gj) {
+    for (int xx = lo; xx <= hi; ++xx) s = fmaf(__ldg(gi + xx), __ldg(gj + xx), s);
+  } else {
+    for (int xx = lo; xx <= hi; ++xx) s += __ldg(gi + xx);
+  }
+  rows[(size_t)m * HW + (size_t)y * W + x] = s;
+}
+
+// ------------------------------------------------------------------- assembly + HGF inverse
+// One thread per pixel. Column sums of the moment rows give the window sums; dividing by N gives
+// the means mu_i = A(G_i) and E_ij = A(G_i G_j). Then S = E - mu mu^T (Sec. 5.1) and Prop. 1 with
+// lambda = eps: for kappa = 0..n-1 (starting from an empty alpha)
+//   u_i   = sum_{j<kappa} alpha_ij S_{j kappa}
+//   gamma = -1 / (1 + S_{kappa kappa} / lambda + sum_{i<kappa} S_{kappa i} u_i)
+//   alpha_ij += gamma u_i u_j (i, j < kappa);  alpha_{i kappa} = gamma u_i / lambda;
+//   alpha_{kappa kappa} = gamma / lambda^2
+// which yields (lambda E + S)^-1 = lambda^-1 E + S alpha (Eq. HGF_w3) = -lambda alpha.
+template <int NG, typename T>
+__global__ void __launch_bounds__(128) k_inverse(const float *__restrict__ rows, int H, int W,
+                                                 int r, double eps, int combine,
+                                                 float *__restrict__ minv,
+                                                 float *__restrict__ mu) {
+  constexpr int P = NG * (NG + 1) / 2;
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y;
+  if (x >= W) return;
+  size_t HW = (size_t)H * W;
+  size_t pix = (size_t)y * W + x;
+  int y0 = max(0, y - r), y1 = min(H - 1, y + r);
+  const T invN = T(1) / T(clipped_count(x, r, W) * (y1 - y0 + 1));
+
+  T m[NG];
+#pragma unroll
+  for (int i = 0; i < NG; ++i) {
+    const float *src = rows + (size_t)i * HW + x;
+    float s = 0.f;
+    for (int yy = y0; yy <= y1; ++yy) s += __ldg(src + (size_t)yy * W);
+    m[i] = T(s) * invN;
+  }
+  T S[P];
+#pragma unroll
+  for (int i = 0; i < NG; ++i) {
+#pragma unroll
+    for (int j = i; j < NG; ++j) {
+      const int e = tri_index(NG, i, j);
+      const float *src = rows + (size_t)(NG + e) * HW + x;
+      float s = 0.f;
+      for (int yy = y0; yy <= y1; ++yy) s += __ldg(src + (size_t)yy * W);
+      S[e] = T(s) * invN - m[i] * m[j];
+    }
+  }
+
+  const T lam = T(eps);
+  const T inv_lam = T(1) / lam;
+  T al[P];
+#pragma unroll
+  for (int e = 0; e < P; ++e) al[e] = T(0);
+#pragma unroll
+  for (int k = 0; k < NG; ++k) {
+    T u[NG > 1 ? NG - 1 : 1];
+#pragma unroll
+    for (int i = 0; i < k; ++i) {
+      T acc = T(0);
+#pragma unroll
+      for (int j = 0; j < k; ++j)
+        acc = fma(al[tri_index(NG, i < j ? i : j, i < j ? j : i)], S[tri_index(NG, j, k)], acc);
+      u[i] = acc;
+    }
+    T den = T(1) + S[tri_index(NG, k, k)] * inv_lam;
+#pragma unroll
+    for (int i = 0; i < k; ++i) den = fma(S[tri_index(NG, i, k)], u[i], den);
+    const T gam = T(-1) / den;
+#pragma unroll
+    for (int i = 0; i < k; ++i) {
+      const T v = gam * u[i];
+#pragma unroll
+      for (int j = i; j < k; ++j) al[tri_index(NG, i, j)] = fma(v, u[j], al[tri_index(NG, i, j)]);
+      al[tri_index(NG, i, k)] = v * inv_lam;
+    }
+    al[tri_index(NG, k, k)] = gam * inv_lam * inv_lam;
+  }
+
+  if (combine == HGF_COMBINE_W3) {
+#pragma unroll
+    for (int i = 0; i < NG; ++i) {
+#pragma unroll
+      for (int j = i; j < NG; ++j) {
+        T acc = (i == j) ? inv_lam : T(0);
+#pragma unroll
+        for (int k = 0; k < NG; ++k)
+          acc = fma(S[tri_index(NG, i < k ? i : k, i < k ? k : i)],
+                    al[tri_index(NG, k < j ? k : j, k < j ? j : k)], acc);
+        minv[(size_t)tri_index(NG, i, j) * HW + pix] = (float)acc;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < P; ++e) minv[(size_t)e * HW + pix] = (float)(-lam * al[e]);
+  }
+#pragma unroll
+  for (int i = 0; i < NG; ++i) mu[(size_t)i * HW + pix] = (float)m[i];
+}
+
+template <int NG, typename T>
+static void launch_inverse_t(const float *rows, const hgf_guidance *g, cudaStream_t s,
+                             Profiler *prof) {
+  dim3 grid((g->W + 127) / 128, g->H);
+  LaunchScope ls(prof, "k_inverse", s);
+  k_inverse<NG, T><<<grid, 128, 0, s>>>(rows, g->H, g->W, g->r, g->eps, g->combine, g->minv,
+                                         g->mu);
+}
+
+template <typename T>
+static bool launch_inverse_n(const float *rows, const hgf_guidance *g, cudaStream_t s,
+                             Profiler *prof) {
+  switch (g->n) {
+#define HGF_INV_CASE(N) \
+  case N:               \
+    launch_inverse_t<N, T>(rows, g, s, prof); \
+    return true;
+    HGF_INV_CASE(1) HGF_INV_CASE(2) HGF_INV_CASE(3) HGF_INV_CASE(4) HGF_INV_CASE(5)
+    HGF_INV_CASE(6) HGF_INV_CASE(7) HGF_INV_CASE(8) HGF_INV_CASE(9) HGF_INV_CASE(19)
+#undef HGF_INV_CASE
+    default:
+      return false;
+  }
+}
+
+size_t prepare_workspace_bytes(int n, int H, int W) {
+  size_t M = (size_t)n + (size_t)n * (n + 1) / 2;
+  size_t rows = M * (size_t)H * W * sizeof(float);
+  size_t part = (size_t)kMeanBlocks * n * sizeof(double);
+  return ((rows + 255) / 256) * 256 + part;
+}
+
+cudaError_t launch_prepare(hgf_guidance *g, const float *img, void *ws, size_t ws_size,
+                           cudaStream_t s, Profiler *prof) {
+  BasisTable bt;
+  if (!make_basis_table(g->C, g->degree, g->basis, &bt) || bt.n != g->n)
+    return cudaErrorInvalidValue;
+  const int H = g->H, W = g->W, n = g->n, HW = H * W;
+  size_t M = (size_t)n + (size_t)n * (n + 1) / 2;
+  if (ws_size < prepare_workspace_bytes(n, H, W)) return cudaErrorInvalidValue;
+  float *rows = (float *)ws;
+  double *partial = (double *)((char *)ws + ((M * HW * sizeof(float) + 255) / 256) * 256);
+
+  {
+    LaunchScope ls(prof, "k_make_guidance", s);
+    k_make_guidance<<<(HW + 255) / 256, 256, 0, s>>>(img, g->C, HW, bt, g->G);
+  }
+  {
+    LaunchScope ls(prof, "k_mean_partial", s);
+    k_mean_partial<<<kMeanBlocks, kMeanThreads, 0, s>>>(g->G, n, HW, partial);
+  }
+  {
+    LaunchScope ls(prof, "k_mean_final", s);
+    k_mean_final<<<1, 32, 0, s>>>(partial, kMeanBlocks, n, HW, g->shift);
+  }
+  {
+    LaunchScope ls(prof, "k_apply_shift", s);
+    k_apply_shift<<<(HW + 255) / 256, 256, 0, s>>>(g->G, g->shift, n, HW);
+  }
+  {
+    dim3 grid_rows((W + 127) / 128, H, (unsigned)M);
+    LaunchScope ls(prof, "k_moment_rows", s);
+    k_moment_rows<<<grid_rows, 128, 0, s>>>(g->G, n, H, W, g->r, rows);
+  }
+  bool ok = g->inv_precision == HGF_F32 ? launch_inverse_n<float>(rows, g, s, prof)
+                                        : launch_inverse_n<double>(rows, g, s, prof);
+  if (!ok) return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------ export
+__global__ void k_export_mu(const float *__restrict__ mu, const float *__restrict__ shift, int n,
+                            int HW, float *__restrict__ out) {
+  size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (p >= (size_t)HW) return;
+  for (int i = 0; i < n; ++i) out[(size_t)i * HW + p] = mu[(size_t)i * HW + p] + shift[i];
+}
+
+cudaError_t launch_export(const hgf_guidance *g, float *minv_out, float *mu_out, cudaStream_t s) {
+  size_t HW = (size_t)g->H * g->W;
+  if (minv_out) {
+    cudaError_t e = cudaMemcpyAsync(minv_out, g->minv, packed_size(g->n) * HW * sizeof(float),
+                                    cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+  }
+  if (mu_out) k_export_mu<<<(unsigned)((HW + 255) / 256), 256, 0, s>>>(g->mu, g->shift, g->n,
+                                                                       (int)HW, mu_out);
+  return cudaGetLastError();
+}
+
+}  // namespace hgf

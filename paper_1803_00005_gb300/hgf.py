@@ -1,0 +1,264 @@
+"""Thin Python binding of libhgf's C ABI (include/hgf.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and passes device pointers
+(``torch.Tensor.data_ptr()``) and the current CUDA stream through unchanged; all computation runs
+in libhgf's kernels. The library must have been built (``paper_1803_00005_gb300.build``); loading
+fails loudly otherwise - there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhgf.so")
+
+HGF_OK, HGF_EINVAL, HGF_ENOMEM, HGF_ECUDA, HGF_ETIMEOUT, HGF_EBUSY, HGF_EAGAIN, \
+    HGF_EUNSUPPORTED = range(8)
+STATUS_NAMES = ["HGF_OK", "HGF_EINVAL", "HGF_ENOMEM", "HGF_ECUDA", "HGF_ETIMEOUT", "HGF_EBUSY",
+                "HGF_EAGAIN", "HGF_EUNSUPPORTED"]
+HGF_F32, HGF_BF16, HGF_F16, HGF_F64 = range(4)
+HGF_BASIS_MONOMIAL, HGF_BASIS_POWERS = range(2)
+HGF_COMBINE_ALPHA, HGF_COMBINE_W3 = range(2)
+
+DTYPE_CODES = {"f32": HGF_F32, "bf16": HGF_BF16, "f16": HGF_F16, "f64": HGF_F64}
+BASIS_CODES = {"monomial": HGF_BASIS_MONOMIAL, "powers": HGF_BASIS_POWERS}
+
+# Every symbol include/hgf.h declares.
+EXPORTED = [
+    "hgf_create", "hgf_destroy", "hgf_last_error", "hgf_num_channels", "hgf_make_guidance",
+    "hgf_prepare", "hgf_guidance_release", "hgf_guidance_info", "hgf_guidance_export",
+    "hgf_aggregate", "hgf_aggregate_plain", "hgf_wta", "hgf_filter_host", "hgf_set_tuning",
+    "hgf_guidance_update", "hgf_launch_count", "hgf_profile_enable", "hgf_profile_report",
+]
+
+
+class HGFError(RuntimeError):
+    def __init__(self, status, msg):
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {msg}")
+        self.status = status
+
+
+class hgf_params(ctypes.Structure):
+    _fields_ = [("degree", ctypes.c_int), ("basis", ctypes.c_int), ("r", ctypes.c_int),
+                ("eps", ctypes.c_double), ("inv_precision", ctypes.c_int),
+                ("combine", ctypes.c_int)]
+
+
+class hgf_tuning(ctypes.Structure):
+    _fields_ = [("labels_per_pass", ctypes.c_int), ("band_rows", ctypes.c_int),
+                ("chunk_labels", ctypes.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """Loads libhgf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_1803_00005_gb300.build` (there is no fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, ip, c_int, c_double = ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double
+    P = ctypes.POINTER
+    sig = {
+        "hgf_create": (c_int, [c_int, P(vp)]),
+        "hgf_destroy": (c_int, [vp]),
+        "hgf_last_error": (ctypes.c_char_p, [vp]),
+        "hgf_num_channels": (c_int, [c_int, c_int, c_int]),
+        "hgf_make_guidance": (c_int, [vp, vp, c_int, c_int, c_int, c_int, c_int, vp, P(c_int), vp]),
+        "hgf_prepare": (c_int, [vp, vp, c_int, c_int, c_int, P(hgf_params), vp, P(vp)]),
+        "hgf_guidance_release": (c_int, [vp]),
+        "hgf_guidance_info": (c_int, [vp, P(c_int), P(c_int), P(c_int), P(c_int), P(c_int),
+                                      P(c_double)]),
+        "hgf_guidance_export": (c_int, [vp, vp, vp, vp, vp]),
+        "hgf_aggregate": (c_int, [vp, vp, vp, c_int, c_int, vp, c_int, vp, vp, vp]),
+        "hgf_aggregate_plain": (c_int, [vp, vp, vp, c_int, c_int, vp, c_int, vp, vp, vp]),
+        "hgf_wta": (c_int, [vp, vp, c_int, c_int, c_int, c_int, vp, vp, vp]),
+        "hgf_filter_host": (c_int, [vp, vp, c_int, c_int, c_int, P(hgf_params), vp, c_int, c_int,
+                                    vp, vp, vp]),
+        "hgf_set_tuning": (c_int, [vp, P(hgf_tuning)]),
+        "hgf_guidance_update": (c_int, [vp, vp, vp, vp]),
+        "hgf_launch_count": (c_int, [vp, P(ctypes.c_ulonglong)]),
+        "hgf_profile_enable": (c_int, [vp, c_int]),
+        "hgf_profile_report": (c_int, [vp, ctypes.c_char_p, ctypes.c_size_t]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check(ctx, st):
+    if st != HGF_OK:
+        msg = lib().hgf_last_error(ctx) if ctx else b""
+        raise HGFError(st, (msg or b"").decode(errors="replace"))
+
+
+def _dtype_code(t):
+    import torch
+    return {torch.float32: HGF_F32, torch.bfloat16: HGF_BF16, torch.float16: HGF_F16,
+            torch.float64: HGF_F64}[t.dtype]
+
+
+def _require_cuda(t, name):
+    if t is not None and (not t.is_cuda or not t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous CUDA tensor")
+
+
+def make_params(degree=1, r=4, eps=1e-4, basis="monomial", inv_precision="f64", combine="alpha"):
+    return hgf_params(degree=int(degree), basis=BASIS_CODES[basis], r=int(r), eps=float(eps),
+                      inv_precision=DTYPE_CODES[inv_precision],
+                      combine=HGF_COMBINE_ALPHA if combine == "alpha" else HGF_COMBINE_W3)
+
+
+# ------------------------------------------------------------------ entry points, same names
+def hgf_create(device=0):
+    h = ctypes.c_void_p()
+    st = lib().hgf_create(int(device), ctypes.byref(h))
+    if st != HGF_OK:
+        raise HGFError(st, f"hgf_create(device={device}) failed")
+    return h
+
+
+def hgf_destroy(ctx):
+    lib().hgf_destroy(ctx)
+
+
+def hgf_last_error(ctx):
+    return (lib().hgf_last_error(ctx) or b"").decode(errors="replace")
+
+
+def hgf_num_channels(C, degree, basis="monomial"):
+    return lib().hgf_num_channels(int(C), int(degree), BASIS_CODES[basis])
+
+
+def hgf_make_guidance(ctx, img, degree, basis="monomial", G_out=None, stream=None):
+    import torch
+    _require_cuda(img, "img")
+    C, H, W = img.shape
+    n = hgf_num_channels(C, degree, basis)
+    if G_out is None:
+        G_out = torch.empty((n, H, W), dtype=torch.float32, device=img.device)
+    n_out = ctypes.c_int()
+    _check(ctx, lib().hgf_make_guidance(ctx, _ptr(img), C, H, W, int(degree), BASIS_CODES[basis],
+                                        _ptr(G_out), ctypes.byref(n_out), _stream(stream)))
+    return G_out
+
+
+def hgf_prepare(ctx, img, params, stream=None):
+    _require_cuda(img, "img")
+    C, H, W = img.shape
+    g = ctypes.c_void_p()
+    _check(ctx, lib().hgf_prepare(ctx, _ptr(img), C, H, W, ctypes.byref(params), _stream(stream),
+                                  ctypes.byref(g)))
+    return g
+
+
+def hgf_guidance_release(g):
+    lib().hgf_guidance_release(g)
+
+
+def hgf_guidance_info(g):
+    v = [ctypes.c_int() for _ in range(5)]
+    eps = ctypes.c_double()
+    st = lib().hgf_guidance_info(g, *[ctypes.byref(x) for x in v], ctypes.byref(eps))
+    if st != HGF_OK:
+        raise HGFError(st, "hgf_guidance_info")
+    C, H, W, n, r = (x.value for x in v)
+    return dict(C=C, H=H, W=W, n=n, r=r, eps=eps.value)
+
+
+def hgf_guidance_export(ctx, g, minv_out=None, mu_out=None, stream=None):
+    _check(ctx, lib().hgf_guidance_export(ctx, g, _ptr(minv_out), _ptr(mu_out), _stream(stream)))
+
+
+def hgf_aggregate(ctx, g, cost, filtered=None, labels=None, best=None, stream=None):
+    for t, nm in ((cost, "cost"), (filtered, "filtered"), (labels, "labels"), (best, "best")):
+        _require_cuda(t, nm)
+    L = cost.shape[0]
+    _check(ctx, lib().hgf_aggregate(ctx, g, _ptr(cost), _dtype_code(cost), L, _ptr(filtered),
+                                    HGF_F32, _ptr(labels), _ptr(best), _stream(stream)))
+
+
+def hgf_aggregate_plain(ctx, g, cost, filtered=None, labels=None, best=None, stream=None):
+    for t, nm in ((cost, "cost"), (filtered, "filtered"), (labels, "labels"), (best, "best")):
+        _require_cuda(t, nm)
+    L = cost.shape[0]
+    _check(ctx, lib().hgf_aggregate_plain(ctx, g, _ptr(cost), _dtype_code(cost), L,
+                                          _ptr(filtered), HGF_F32, _ptr(labels), _ptr(best),
+                                          _stream(stream)))
+
+
+def hgf_wta(ctx, filtered, labels=None, best=None, stream=None):
+    _require_cuda(filtered, "filtered")
+    L, H, W = filtered.shape
+    _check(ctx, lib().hgf_wta(ctx, _ptr(filtered), HGF_F32, L, H, W, _ptr(labels), _ptr(best),
+                              _stream(stream)))
+
+
+def hgf_filter_host(ctx, img, cost, cost_dtype, params, labels, best=None, stream=None):
+    """img: numpy float32 (C, H, W); cost: numpy (L, H, W) raw storage (float32, float16 or
+    bf16 bits as uint16); labels: numpy int32 (H, W); best: numpy float32 (H, W) or None.
+    Host buffers may be pinned (e.g. numpy views of pinned torch tensors)."""
+    import numpy as np
+    C, H, W = img.shape
+    L = cost.shape[0]
+    for a in (img, cost, labels, best):
+        if a is not None and not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be C-contiguous")
+    assert img.dtype == np.float32 and labels.dtype == np.int32
+    st = lib().hgf_filter_host(ctx, ctypes.c_void_p(img.ctypes.data), C, H, W,
+                               ctypes.byref(params), ctypes.c_void_p(cost.ctypes.data),
+                               DTYPE_CODES[cost_dtype], L,
+                               ctypes.c_void_p(labels.ctypes.data),
+                               None if best is None else ctypes.c_void_p(best.ctypes.data),
+                               _stream(stream))
+    _check(ctx, st)
+
+
+def hgf_set_tuning(ctx, labels_per_pass=0, band_rows=0, chunk_labels=0):
+    t = hgf_tuning(labels_per_pass=labels_per_pass, band_rows=band_rows,
+                   chunk_labels=chunk_labels)
+    _check(ctx, lib().hgf_set_tuning(ctx, ctypes.byref(t)))
+
+
+def hgf_guidance_update(ctx, g, img, stream=None):
+    _require_cuda(img, "img")
+    _check(ctx, lib().hgf_guidance_update(ctx, g, _ptr(img), _stream(stream)))
+
+
+def hgf_launch_count(ctx):
+    v = ctypes.c_ulonglong()
+    _check(ctx, lib().hgf_launch_count(ctx, ctypes.byref(v)))
+    return v.value
+
+
+def hgf_profile_enable(ctx, enable=True):
+    _check(ctx, lib().hgf_profile_enable(ctx, 1 if enable else 0))
+
+
+def hgf_profile_report(ctx):
+    import json
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(ctx, lib().hgf_profile_report(ctx, buf, len(buf)))
+    return json.loads(buf.value.decode())
