@@ -56,7 +56,7 @@ def flops_per_unit(kernel: str, n: int) -> tuple[float, str] | None:
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["fused", "plain", "reference"], default="fused")
     ap.add_argument("--workload", choices=list(WORKLOADS), default="quarter")

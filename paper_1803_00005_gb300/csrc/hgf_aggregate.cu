@@ -1,18 +1,21 @@
 // Fused multi-label aggregation + WTA (Sec. 1 pipeline with the centred form of Sec. 5.1 and the
 // multipoint aggregation of Sec. 4.1, Eq. HGF_z1).
 //
-// Two streaming kernels per chunk of labels, both over vertical strips of the image:
-//   k_coef : per input row, float32 vertical running sums of (p, G_1 p, .., G_n p) for K labels,
-//            horizontal window sums by a prefix scan in shared memory, then per coefficient pixel
-//            cov = A(G p) - mu A(p), a = Minv cov, b = A(p) - a.mu. Each cost element is read from
-//            device memory once (plus its halo columns) and the resident inverse once per K labels.
-//   k_apply: per coefficient row, vertical running sums of (b, a_1..a_n), horizontal window sums,
-//            q = sum_i A(a_i) G_i + A(b), minimum over the CTA's labels and one packed 64-bit
-//            atomicMin per pixel (cost in the high word, label in the low word: lowest cost, then
-//            lowest label).
+// Two streaming kernels per chunk of labels, both over vertical strips of the image (128 columns
+// per CTA, one thread per column, 2r of them halo) that walk down a band of rows:
+//   k_coef : vertical running sums of (p, G_1 p, .., G_n p) for K labels, horizontal window sums
+//            by prefix scans in shared memory, then per coefficient pixel
+//            cov = A(G p) - mu A(p), a = Minv cov, b = A(p) - a.mu, written to the workspace.
+//            The guidance G is recomputed from the input image (constant-index monomials).
+//   k_apply: vertical running sums of (b, a_1..a_n), horizontal window sums,
+//            q = sum_i A(a_i) G_i + A(b), and one packed 64-bit atomicMin per pixel (cost in the
+//            high word, label in the low word: lowest cost, then lowest label).
+// Every input row is read from device memory once: each thread keeps its column's last 2r+1 rows
+// in a private shared-memory ring (the row leaving the vertical window is subtracted from there)
+// and loads rows two steps ahead into registers, so the load latency overlaps two steps of work.
 // Windows are clipped at the image border: samples outside the image never enter a sum and the
 // means divide by the in-image count N(x, y).
-#include "hgf_internal.cuh"
+#include "hgf_basis.cuh"
 
 #include <algorithm>
 
@@ -47,15 +50,32 @@ __device__ __forceinline__ void scan_rows(float *sA, int rows) {
   }
 }
 
-template <int NG, int K, typename CT>
+// Window sum [t, t + 2r] of a scanned shared row.
+__device__ __forceinline__ float window(const float *row, int t, int r) {
+  return row[4 + t + 2 * r] - row[3 + t];
+}
+
+template <int B, int K>
+constexpr size_t coef_smem_bytes(int r) {
+  return sizeof(float) * ((size_t)K * (basis_n(B) + 1) * kRowStride +
+                          (size_t)(2 * r + 1) * (basis_channels_in(B) + K) * NT);
+}
+
+template <int B, int K, typename CT>
 __global__ void __launch_bounds__(NT) k_coef(const CT *__restrict__ cost, int H, int W, int r,
-                                             const float *__restrict__ G,
+                                             const float *__restrict__ img,
+                                             const float *__restrict__ shift,
                                              const float *__restrict__ minv,
                                              const float *__restrict__ mu,
                                              float *__restrict__ coef, int l_first, int n_chunk,
                                              int band_rows) {
-  constexpr int C1 = NG + 1;
-  __shared__ __align__(16) float sA[K * C1 * kRowStride];
+  constexpr int NG = basis_n(B), C1 = NG + 1, NC = basis_channels_in(B), RAW = NC + K;
+  constexpr int P = NG * (NG + 1) / 2;
+  constexpr bool EARLY = P <= 64;  // the inverse fits in registers: load it ahead of the scans
+  extern __shared__ __align__(16) float smem[];
+  float *sA = smem;
+  float *ring = smem + K * C1 * kRowStride;  // [2r+1][RAW][NT], thread-private columns
+  const int R = 2 * r + 1;
   const size_t HW = (size_t)H * W;
   const int t = threadIdx.x;
   const int TW = NT - 2 * r;
@@ -67,8 +87,29 @@ __global__ void __launch_bounds__(NT) k_coef(const CT *__restrict__ cost, int H,
   const int k0 = blockIdx.z * K;
   const int nk = min(K, n_chunk - k0);
   const int add_lo = max(0, Y0 - r);
+  const int s_begin = Y0 - r, s_end = Y1 + r;
 
   for (int i = t; i < K * C1; i += NT) sA[i * kRowStride + 3] = 0.f;
+  float sh[NG];
+#pragma unroll
+  for (int i = 0; i < NG; ++i) sh[i] = __ldg(shift + i);
+
+  const CT *cbase = cost + (size_t)(l_first + k0) * HW;
+  auto load_row = [&](int row, float *v) {
+    if (col_ok && row >= 0 && row < H) {
+      const size_t pix = (size_t)row * W + xi;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) v[c] = __ldg(img + (size_t)c * HW + pix);
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        v[NC + k] = k < nk ? load_cost(cbase, (size_t)k * HW + pix) : 0.f;
+    }
+  };
+  float pa[RAW], pb[RAW], pc[RAW];
+#pragma unroll
+  for (int c = 0; c < RAW; ++c) pa[c] = pb[c] = pc[c] = 0.f;
+  load_row(s_begin, pa);
+  load_row(s_begin + 1, pb);
 
   float V[K][C1];
 #pragma unroll
@@ -76,44 +117,57 @@ __global__ void __launch_bounds__(NT) k_coef(const CT *__restrict__ cost, int H,
 #pragma unroll
     for (int c = 0; c < C1; ++c) V[k][c] = 0.f;
 
-  const CT *cbase = cost + (size_t)(l_first + k0) * HW;
-
-  for (int s = Y0 - r; s < Y1 + r; ++s) {
+  for (int s = s_begin; s < s_end; ++s) {
+    load_row(s + 2, pc);  // consumed two steps later
+    const int y1 = s - r;
+    const int x = x0 + t;
+    const bool coef_here = y1 >= Y0 && t < TW && x < W;
+    float Mreg[EARLY ? P : 1], m[NG];
+    if (coef_here) {  // issued now, used after the scans: the latency overlaps phases A and B
+      const size_t pix = (size_t)y1 * W + x;
+#pragma unroll
+      for (int i = 0; i < NG; ++i) m[i] = __ldg(mu + (size_t)i * HW + pix);
+      if (EARLY) {
+#pragma unroll
+        for (int e = 0; e < (EARLY ? P : 1); ++e) Mreg[e] = __ldg(minv + (size_t)e * HW + pix);
+      }
+    }
     // ---- phase A: vertical running sums over input rows [s-2r, s]
     if (col_ok) {
-      if (s >= 0 && s < H) {
-        const size_t pix = (size_t)s * W + xi;
-        float g[NG];
+      float *slot = ring + (size_t)(((s - s_begin) % R) * RAW) * NT + t;
+      const int so = s - 2 * r - 1;
+      if (so >= add_lo) {  // the outgoing row occupies the slot the new row will take
+        float xo[NC], go[NG];
 #pragma unroll
-        for (int i = 0; i < NG; ++i) g[i] = __ldg(G + (size_t)i * HW + pix);
+        for (int c = 0; c < NC; ++c) xo[c] = slot[c * NT];
+        eval_basis<B>(xo, sh, go);
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-          if (k < nk) {
-            const float p = load_cost(cbase, (size_t)k * HW + pix);
-            V[k][0] += p;
+          const float p = slot[(NC + k) * NT];
+          V[k][0] -= p;
 #pragma unroll
-            for (int i = 0; i < NG; ++i) V[k][i + 1] = fmaf(g[i], p, V[k][i + 1]);
-          }
+          for (int i = 0; i < NG; ++i) V[k][i + 1] = fmaf(-go[i], p, V[k][i + 1]);
         }
       }
-      const int so = s - 2 * r - 1;
-      if (so >= add_lo) {
-        const size_t pix = (size_t)so * W + xi;
+      if (s >= 0 && s < H) {
         float g[NG];
+        eval_basis<B>(pa, sh, g);
 #pragma unroll
-        for (int i = 0; i < NG; ++i) g[i] = __ldg(G + (size_t)i * HW + pix);
+        for (int c = 0; c < RAW; ++c) slot[c * NT] = pa[c];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-          if (k < nk) {
-            const float p = load_cost(cbase, (size_t)k * HW + pix);
-            V[k][0] -= p;
+          const float p = pa[NC + k];
+          V[k][0] += p;
 #pragma unroll
-            for (int i = 0; i < NG; ++i) V[k][i + 1] = fmaf(-g[i], p, V[k][i + 1]);
-          }
+          for (int i = 0; i < NG; ++i) V[k][i + 1] = fmaf(g[i], p, V[k][i + 1]);
         }
       }
     }
-    const int y1 = s - r;
+#pragma unroll
+    for (int c = 0; c < RAW; ++c) {
+      pa[c] = pb[c];
+      pb[c] = pc[c];
+    }
     if (y1 < Y0) continue;  // warm-up rows: no coefficient row complete yet (uniform per CTA)
 
     // ---- phase B: horizontal window sums via inclusive prefix scans
@@ -125,23 +179,18 @@ __global__ void __launch_bounds__(NT) k_coef(const CT *__restrict__ cost, int H,
     scan_rows(sA, nk * C1);
     __syncthreads();
 
-    // ---- phase C: coefficients at (x0 + t, y1)
-    const int x = x0 + t;
-    if (t < TW && x < W) {
+    // ---- phase C: coefficients at (x, y1)
+    if (coef_here) {
       const size_t pix = (size_t)y1 * W + x;
       const float invN = 1.f / (float)(clipped_count(x, r, W) * clipped_count(y1, r, H));
-      float m[NG];
-#pragma unroll
-      for (int i = 0; i < NG; ++i) m[i] = __ldg(mu + (size_t)i * HW + pix);
       float cov[K][NG], a[K][NG], pbar[K];
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const float *row = sA + k * C1 * kRowStride;
-        pbar[k] = (row[4 + t + 2 * r] - row[3 + t]) * invN;
+        pbar[k] = window(row, t, r) * invN;
 #pragma unroll
         for (int i = 0; i < NG; ++i) {
-          const float *ri = row + (i + 1) * kRowStride;
-          const float mi = (ri[4 + t + 2 * r] - ri[3 + t]) * invN;
+          const float mi = window(row + (i + 1) * kRowStride, t, r) * invN;
           cov[k][i] = fmaf(-m[i], pbar[k], mi);
           a[k][i] = 0.f;
         }
@@ -150,7 +199,8 @@ __global__ void __launch_bounds__(NT) k_coef(const CT *__restrict__ cost, int H,
       for (int i = 0; i < NG; ++i) {
 #pragma unroll
         for (int j = i; j < NG; ++j) {
-          const float Mij = __ldg(minv + (size_t)tri_index(NG, i, j) * HW + pix);
+          const float Mij = EARLY ? Mreg[EARLY ? tri_index(NG, i, j) : 0]
+                                  : __ldg(minv + (size_t)tri_index(NG, i, j) * HW + pix);
 #pragma unroll
           for (int k = 0; k < K; ++k) {
             a[k][i] = fmaf(Mij, cov[k][j], a[k][i]);
@@ -175,14 +225,26 @@ __global__ void __launch_bounds__(NT) k_coef(const CT *__restrict__ cost, int H,
   }
 }
 
-template <int NG, int K>
+template <int B, bool RING>
+constexpr size_t apply_smem_bytes(int r) {
+  return sizeof(float) * ((size_t)(basis_n(B) + 1) * kRowStride +
+                          (RING ? (size_t)(2 * r + 1) * (basis_n(B) + 1) * NT : 0));
+}
+
+// One label per CTA. RING: the outgoing coefficient row comes from the thread's shared-memory
+// ring; otherwise it is reloaded from device memory (used when the ring does not fit).
+template <int B, bool RING>
 __global__ void __launch_bounds__(NT) k_apply(const float *__restrict__ coef, int H, int W, int r,
-                                              const float *__restrict__ G,
+                                              const float *__restrict__ img,
+                                              const float *__restrict__ shift,
                                               unsigned long long *__restrict__ keys,
                                               float *__restrict__ filtered, int l_first,
-                                              int n_chunk, int band_rows) {
-  constexpr int C1 = NG + 1;
-  __shared__ __align__(16) float sA[K * C1 * kRowStride];
+                                              int band_rows) {
+  constexpr int NG = basis_n(B), C1 = NG + 1, NC = basis_channels_in(B);
+  extern __shared__ __align__(16) float smem[];
+  float *sA = smem;
+  float *ring = smem + C1 * kRowStride;  // [2r+1][C1][NT]
+  const int R = 2 * r + 1;
   const size_t HW = (size_t)H * W;
   const int t = threadIdx.x;
   const int TW = NT - 2 * r;
@@ -191,82 +253,93 @@ __global__ void __launch_bounds__(NT) k_apply(const float *__restrict__ coef, in
   const bool col_ok = xc >= 0 && xc < W;
   const int Y0 = blockIdx.y * band_rows;
   const int Y1 = min(H, Y0 + band_rows);
-  const int k0 = blockIdx.z * K;
-  const int nk = min(K, n_chunk - k0);
+  const int k = blockIdx.z;
   const int add_lo = max(0, Y0 - r);
+  const int s_begin = Y0 - r, s_end = Y1 + r;
 
-  for (int i = t; i < K * C1; i += NT) sA[i * kRowStride + 3] = 0.f;
-
-  float V[K][C1];
+  if (t < C1) sA[t * kRowStride + 3] = 0.f;
+  const float *cb = coef + (size_t)k * C1 * HW;
+  auto load_row = [&](int row, float *v) {
+    if (col_ok && row >= 0 && row < H) {
+      const size_t pix = (size_t)row * W + xc;
 #pragma unroll
-  for (int k = 0; k < K; ++k)
+      for (int c = 0; c < C1; ++c) v[c] = __ldg(cb + (size_t)c * HW + pix);
+    }
+  };
+  float pa[C1], pb[C1], pc[C1];
 #pragma unroll
-    for (int c = 0; c < C1; ++c) V[k][c] = 0.f;
+  for (int c = 0; c < C1; ++c) pa[c] = pb[c] = pc[c] = 0.f;
+  load_row(s_begin, pa);
+  load_row(s_begin + 1, pb);
+  float V[C1];
+#pragma unroll
+  for (int c = 0; c < C1; ++c) V[c] = 0.f;
 
-  const float *cb = coef + (size_t)k0 * C1 * HW;
-
-  for (int s = Y0 - r; s < Y1 + r; ++s) {
+  for (int s = s_begin; s < s_end; ++s) {
+    load_row(s + 2, pc);
+    const int y2 = s - r;
+    const int x = x0 + t;
+    const bool out_here = y2 >= Y0 && t < TW && x < W;
+    float xin[NC];
+    if (out_here) {
+      const size_t pix = (size_t)y2 * W + x;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) xin[c] = __ldg(img + (size_t)c * HW + pix);
+    }
     if (col_ok) {
-      if (s >= 0 && s < H) {
-        const size_t pix = (size_t)s * W + xc;
-#pragma unroll
-        for (int k = 0; k < K; ++k)
-          if (k < nk) {
-#pragma unroll
-            for (int c = 0; c < C1; ++c) V[k][c] += __ldg(cb + (size_t)(k * C1 + c) * HW + pix);
-          }
-      }
       const int so = s - 2 * r - 1;
-      if (so >= add_lo) {
-        const size_t pix = (size_t)so * W + xc;
+      if (RING) {
+        float *slot = ring + (size_t)(((s - s_begin) % R) * C1) * NT + t;
+        if (so >= add_lo) {
 #pragma unroll
-        for (int k = 0; k < K; ++k)
-          if (k < nk) {
+          for (int c = 0; c < C1; ++c) V[c] -= slot[c * NT];
+        }
+        if (s >= 0 && s < H) {
 #pragma unroll
-            for (int c = 0; c < C1; ++c) V[k][c] -= __ldg(cb + (size_t)(k * C1 + c) * HW + pix);
+          for (int c = 0; c < C1; ++c) {
+            V[c] += pa[c];
+            slot[c * NT] = pa[c];
           }
+        }
+      } else {
+        if (so >= add_lo) {
+          const size_t pix = (size_t)so * W + xc;
+#pragma unroll
+          for (int c = 0; c < C1; ++c) V[c] -= __ldg(cb + (size_t)c * HW + pix);
+        }
+        if (s >= 0 && s < H) {
+#pragma unroll
+          for (int c = 0; c < C1; ++c) V[c] += pa[c];
+        }
       }
     }
-    const int y2 = s - r;
+#pragma unroll
+    for (int c = 0; c < C1; ++c) {
+      pa[c] = pb[c];
+      pb[c] = pc[c];
+    }
     if (y2 < Y0) continue;
 
 #pragma unroll
-    for (int k = 0; k < K; ++k)
-#pragma unroll
-      for (int c = 0; c < C1; ++c) sA[(k * C1 + c) * kRowStride + 4 + t] = V[k][c];
+    for (int c = 0; c < C1; ++c) sA[c * kRowStride + 4 + t] = V[c];
     __syncthreads();
-    scan_rows(sA, nk * C1);
+    scan_rows(sA, C1);
     __syncthreads();
 
-    const int x = x0 + t;
-    if (t < TW && x < W) {
+    if (out_here) {
       const size_t pix = (size_t)y2 * W + x;
       const float invN = 1.f / (float)(clipped_count(x, r, W) * clipped_count(y2, r, H));
-      float g[NG];
+      float sh[NG], g[NG];
 #pragma unroll
-      for (int i = 0; i < NG; ++i) g[i] = __ldg(G + (size_t)i * HW + pix);
-      float qbest = 0.f;
-      int kbest = -1;
+      for (int i = 0; i < NG; ++i) sh[i] = __ldg(shift + i);
+      eval_basis<B>(xin, sh, g);
+      float q = window(sA, t, r);
 #pragma unroll
-      for (int k = 0; k < K; ++k) {
-        if (k < nk) {
-          const float *row = sA + k * C1 * kRowStride;
-          float q = row[4 + t + 2 * r] - row[3 + t];
-#pragma unroll
-          for (int i = 0; i < NG; ++i) {
-            const float *ri = row + (i + 1) * kRowStride;
-            q = fmaf(ri[4 + t + 2 * r] - ri[3 + t], g[i], q);
-          }
-          q *= invN;
-          if (filtered) filtered[(size_t)(l_first + k0 + k) * HW + pix] = q;
-          const float qk = (q != q) ? __int_as_float(0x7f800000) : q;
-          if (kbest < 0 || qk < qbest) {
-            qbest = qk;
-            kbest = k;
-          }
-        }
-      }
-      if (keys) atomicMin(keys + pix, wta_key(qbest, l_first + k0 + kbest));
+      for (int i = 0; i < NG; ++i) q = fmaf(window(sA + (i + 1) * kRowStride, t, r), g[i], q);
+      q *= invN;
+      const int label = l_first + k;
+      if (filtered) filtered[(size_t)label * HW + pix] = q;
+      if (keys) atomicMin(keys + pix, wta_key(q, label));
     }
     __syncthreads();
   }
@@ -300,37 +373,53 @@ __global__ void k_wta_volume(const float *__restrict__ q, int L, int HW,
   if (best) best[p] = b;
 }
 
-template <int NG, int K>
+template <typename Kern>
+cudaError_t set_smem(Kern k, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int B, int K>
 cudaError_t launch_chunk(const hgf_guidance *g, const void *cost, int cost_dtype, int l_first,
                          int nc, float *filtered, float *coef_ws, unsigned long long *keys,
                          int band_rows, cudaStream_t s, Profiler *prof) {
   const int H = g->H, W = g->W, r = g->r;
   const int TW = NT - 2 * r;
-  dim3 grid((W + TW - 1) / TW, (H + band_rows - 1) / band_rows, (nc + K - 1) / K);
+  const unsigned strips = (W + TW - 1) / TW, bands = (H + band_rows - 1) / band_rows;
+  cudaError_t e;
   {
-  LaunchScope ls(prof, "k_coef", s);
-  switch (cost_dtype) {
-    case HGF_F32:
-      k_coef<NG, K, float><<<grid, NT, 0, s>>>((const float *)cost, H, W, r, g->G, g->minv, g->mu,
-                                               coef_ws, l_first, nc, band_rows);
-      break;
-    case HGF_BF16:
-      k_coef<NG, K, __nv_bfloat16><<<grid, NT, 0, s>>>((const __nv_bfloat16 *)cost, H, W, r,
-                                                       g->G, g->minv, g->mu, coef_ws, l_first,
-                                                       nc, band_rows);
-      break;
-    case HGF_F16:
-      k_coef<NG, K, __half><<<grid, NT, 0, s>>>((const __half *)cost, H, W, r, g->G, g->minv,
-                                                g->mu, coef_ws, l_first, nc, band_rows);
-      break;
-    default:
-      return cudaErrorInvalidValue;
-  }
+    dim3 grid(strips, bands, (nc + K - 1) / K);
+    const size_t sm = coef_smem_bytes<B, K>(r);
+    LaunchScope ls(prof, "k_coef", s);
+#define HGF_COEF(CT)                                                                          \
+  e = set_smem(k_coef<B, K, CT>, sm);                                                         \
+  if (e != cudaSuccess) return e;                                                             \
+  k_coef<B, K, CT><<<grid, NT, sm, s>>>((const CT *)cost, H, W, r, g->img, g->shift, g->minv, \
+                                        g->mu, coef_ws, l_first, nc, band_rows);
+    switch (cost_dtype) {
+      case HGF_F32: HGF_COEF(float) break;
+      case HGF_BF16: HGF_COEF(__nv_bfloat16) break;
+      case HGF_F16: HGF_COEF(__half) break;
+      default: return cudaErrorInvalidValue;
+    }
+#undef HGF_COEF
   }
   {
+    dim3 grid(strips, bands, nc);
     LaunchScope ls(prof, "k_apply", s);
-    k_apply<NG, K><<<grid, NT, 0, s>>>(coef_ws, H, W, r, g->G, keys, filtered, l_first, nc,
-                                       band_rows);
+    const size_t ring_sm = apply_smem_bytes<B, true>(r);
+    if (ring_sm <= 110 * 1024) {  // two CTAs per SM
+      e = set_smem(k_apply<B, true>, ring_sm);
+      if (e != cudaSuccess) return e;
+      k_apply<B, true><<<grid, NT, ring_sm, s>>>(coef_ws, H, W, r, g->img, g->shift, keys,
+                                                 filtered, l_first, band_rows);
+    } else {
+      const size_t sm = apply_smem_bytes<B, false>(r);
+      e = set_smem(k_apply<B, false>, sm);
+      if (e != cudaSuccess) return e;
+      k_apply<B, false><<<grid, NT, sm, s>>>(coef_ws, H, W, r, g->img, g->shift, keys, filtered,
+                                             l_first, band_rows);
+    }
   }
   return cudaGetLastError();
 }
@@ -346,11 +435,23 @@ bool aggregate_supported(int n) {
   }
 }
 
-static int labels_per_pass_for(int n) { return n >= 19 ? 2 : 4; }
+// Dynamic shared memory of k_coef for n guidance channels, C input channels, K labels, radius r.
+static size_t coef_smem(int n, int C, int K, int r) {
+  return sizeof(float) * ((size_t)K * (n + 1) * kRowStride + (size_t)(2 * r + 1) * (C + K) * NT);
+}
+
+bool aggregate_fits(const hgf_guidance *g) {
+  return 2 * g->r + 1 < NT && coef_smem(g->n, g->C, 2, g->r) <= 227 * 1024;
+}
 
 AggregatePlan plan_aggregate(const hgf_guidance *g, int L, const hgf_tuning &t, int num_sms) {
   AggregatePlan p;
-  p.K = labels_per_pass_for(g->n);
+  // four labels per pass while two CTAs still fit on an SM, else two
+  const bool four_fits = g->n < 19 && coef_smem(g->n, g->C, 4, g->r) <= 113 * 1024;
+  p.K = four_fits ? 4 : 2;
+  if (t.labels_per_pass == 2 || (t.labels_per_pass == 4 &&
+                                 coef_smem(g->n, g->C, 4, g->r) <= 227 * 1024))
+    p.K = t.labels_per_pass;
   const size_t plane = (size_t)(g->n + 1) * g->H * g->W * sizeof(float);
   // labels per chunk: all labels while the coefficient workspace stays under 4 GiB
   size_t cap = std::max<size_t>(1, ((size_t)4 << 30) / plane);
@@ -362,7 +463,8 @@ AggregatePlan plan_aggregate(const hgf_guidance *g, int L, const hgf_tuning &t, 
   if (t.band_rows > 0) {
     p.band_rows = t.band_rows;
   } else {
-    // about 2 CTAs per SM, but bands of at least 4r rows so the warm-up rows stay a fraction
+    // about 2 CTAs per SM for the coefficient kernel, with bands of at least 4r rows so the
+    // warm-up rows stay a fraction of the work
     const int target = 2 * std::max(1, num_sms);
     int bands = std::max(1, (target + strips * passes - 1) / (strips * passes));
     int rows = (g->H + bands - 1) / bands;
@@ -373,27 +475,6 @@ AggregatePlan plan_aggregate(const hgf_guidance *g, int L, const hgf_tuning &t, 
 
 size_t aggregate_coef_bytes(const hgf_guidance *g, const AggregatePlan &p) {
   return (size_t)p.chunk * (g->n + 1) * g->H * g->W * sizeof(float);
-}
-
-template <int NG>
-static cudaError_t run_chunks(const hgf_guidance *g, const void *cost, int cost_dtype, int L,
-                              float *filtered, float *coef_ws, unsigned long long *keys,
-                              const AggregatePlan &p, cudaStream_t s, Profiler *prof) {
-  for (int l0 = 0; l0 < L; l0 += p.chunk) {
-    int nc = std::min(p.chunk, L - l0);
-    cudaError_t e;
-    if (p.K == 4)
-      e = launch_chunk<NG, 4>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys, p.band_rows,
-                              s, prof);
-    else if (p.K == 2)
-      e = launch_chunk<NG, 2>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys, p.band_rows,
-                              s, prof);
-    else
-      e = launch_chunk<NG, 1>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys, p.band_rows,
-                              s, prof);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
 }
 
 cudaError_t launch_aggregate(const hgf_guidance *g, const void *cost, int cost_dtype, int L,
@@ -407,18 +488,22 @@ cudaError_t launch_aggregate(const hgf_guidance *g, const void *cost, int cost_d
     cudaError_t e = cudaMemsetAsync(k, 0xff, (size_t)HW * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
   }
-  cudaError_t e;
-  switch (g->n) {
-#define HGF_AGG_CASE(N)                                                                   \
-  case N:                                                                                 \
-    e = run_chunks<N>(g, cost, cost_dtype, L, filtered, coef_ws, k, p, s, prof);          \
-    break;
-    HGF_AGG_CASE(1) HGF_AGG_CASE(2) HGF_AGG_CASE(3) HGF_AGG_CASE(4) HGF_AGG_CASE(5)
-    HGF_AGG_CASE(6) HGF_AGG_CASE(7) HGF_AGG_CASE(8) HGF_AGG_CASE(9) HGF_AGG_CASE(19)
-#undef HGF_AGG_CASE
-    default:
-      return cudaErrorInvalidValue;
-  }
+  const int b = basis_id(g->C, g->degree, g->basis);
+  cudaError_t e = cudaErrorInvalidValue;
+  bool ok = dispatch_basis(b, [&](auto bc) {
+    constexpr int B = decltype(bc)::value;
+    e = cudaSuccess;
+    for (int l0 = 0; l0 < L && e == cudaSuccess; l0 += p.chunk) {
+      const int nc = std::min(p.chunk, L - l0);
+      if (p.K == 4)
+        e = launch_chunk<B, 4>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, k, p.band_rows, s,
+                               prof);
+      else
+        e = launch_chunk<B, 2>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, k, p.band_rows, s,
+                               prof);
+    }
+  });
+  if (!ok) return cudaErrorInvalidValue;
   if (e != cudaSuccess) return e;
   if (k) {
     LaunchScope ls(prof, "k_wta_finalize", s);

@@ -130,7 +130,7 @@ hgf_status alloc_guidance(hgf_ctx *ctx, int C, int H, int W, int n, const hgf_pa
   g->inv_precision = p->inv_precision;
   g->combine = p->combine;
   const size_t HW = (size_t)H * W;
-  const size_t floats = HW * ((size_t)n + packed_size(n) + n) + 64;
+  const size_t floats = HW * ((size_t)C + n + packed_size(n) + n) + 64;
   float *base = nullptr;
   cudaError_t e = cudaMalloc(&base, floats * sizeof(float));
   if (e != cudaSuccess) {
@@ -139,7 +139,8 @@ hgf_status alloc_guidance(hgf_ctx *ctx, int C, int H, int W, int n, const hgf_pa
     return set_err(ctx, HGF_ENOMEM, "cannot allocate %zu bytes for the guidance",
                    floats * sizeof(float));
   }
-  g->G = base;
+  g->img = base;
+  g->G = g->img + (size_t)C * HW;
   g->minv = g->G + (size_t)n * HW;
   g->mu = g->minv + (size_t)packed_size(n) * HW;
   g->shift = g->mu + (size_t)n * HW;
@@ -182,12 +183,21 @@ hgf_status check_outputs(hgf_ctx *ctx, const hgf_guidance *g, const void *cost, 
 hgf_status aggregate_locked(hgf_ctx *ctx, const hgf_guidance *g, const void *cost,
                             int cost_dtype, int L, void *filtered, int32_t *labels, float *best,
                             cudaStream_t s) {
-  if (2 * g->r + 1 > kStripThreads) {
-    ctx->err = "fused path needs 2r+1 < " + std::to_string(kStripThreads);
-    return HGF_EUNSUPPORTED;
+  if (!aggregate_fits(g)) {
+    // windows too wide for the streaming kernels' shared-memory rings: the plain kernels
+    // compute the same result for any radius
+    int chunk = 1;
+    size_t need = plain_workspace_bytes(g, L, &chunk);
+    const size_t qbytes = filtered ? 0 : (size_t)L * g->H * g->W * sizeof(float);
+    hgf_status st = grow(ctx, ctx->ws_plain, need + qbytes, s);
+    if (st != HGF_OK) return st;
+    float *q = filtered ? (float *)filtered : (float *)((char *)ctx->ws_plain.ptr + need);
+    cudaError_t e = launch_aggregate_plain(g, cost, cost_dtype, L, q, labels, best,
+                                           ctx->ws_plain.ptr, chunk, s, &ctx->prof);
+    if (e != cudaSuccess) return cuda_fail_locked(ctx, e, "hgf_aggregate (wide window)");
+    return HGF_OK;
   }
   AggregatePlan plan = plan_aggregate(g, L, ctx->tuning, ctx->num_sms);
-  if (ctx->tuning.labels_per_pass > 0) plan.K = ctx->tuning.labels_per_pass;
   hgf_status st = grow(ctx, ctx->ws_coef, aggregate_coef_bytes(g, plan), s);
   if (st == HGF_OK)
     st = grow(ctx, ctx->ws_keys, (size_t)g->H * g->W * sizeof(unsigned long long), s);
@@ -234,7 +244,7 @@ hgf_status hgf_destroy(hgf_ctx *ctx) {
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
   if (ctx->host_guidance) {
-    cudaFree(ctx->host_guidance->G);
+    cudaFree(ctx->host_guidance->img);
     delete ctx->host_guidance;
   }
   for (auto &rec : ctx->prof.recs) {
@@ -287,7 +297,7 @@ hgf_status hgf_prepare(hgf_ctx *ctx, const float *img, int C, int H, int W,
     st = prepare_locked(ctx, g, img, (cudaStream_t)stream);
   }
   if (st != HGF_OK) {
-    cudaFree(g->G);
+    cudaFree(g->img);
     delete g;
     return st;
   }
@@ -298,7 +308,7 @@ hgf_status hgf_prepare(hgf_ctx *ctx, const float *img, int C, int H, int W,
 hgf_status hgf_guidance_release(hgf_guidance *g) {
   if (!g) return HGF_OK;
   cudaSetDevice(g->ctx->device);
-  cudaFree(g->G);
+  cudaFree(g->img);
   delete g;
   return HGF_OK;
 }
@@ -416,7 +426,7 @@ hgf_status hgf_filter_host(hgf_ctx *ctx, const float *img, int C, int H, int W,
   if (!same_shape(ctx->host_guidance, C, H, W, params)) {
     if (ctx->host_guidance) {
       cudaStreamSynchronize(s);
-      cudaFree(ctx->host_guidance->G);
+      cudaFree(ctx->host_guidance->img);
       delete ctx->host_guidance;
       ctx->host_guidance = nullptr;
     }

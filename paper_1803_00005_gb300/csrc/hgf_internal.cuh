@@ -9,6 +9,7 @@
 #include <atomic>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/hgf.h"
@@ -146,6 +147,7 @@ struct hgf_guidance {
   int C = 0, H = 0, W = 0, n = 0, degree = 0, basis = 0, r = 0;
   double eps = 0.0;
   int inv_precision = HGF_F64, combine = HGF_COMBINE_ALPHA;
+  float *img = nullptr;    // C x H x W, copy of the input image
   float *G = nullptr;      // n x H x W, shifted guidance G_i - c_i
   float *minv = nullptr;   // n(n+1)/2 x H x W, packed (Sigma + eps E)^-1
   float *mu = nullptr;     // n x H x W, shifted means A(G_i) - c_i
@@ -180,5 +182,6 @@ cudaError_t launch_aggregate_plain(const hgf_guidance *g, const void *cost, int 
 cudaError_t launch_wta(const float *filtered, int L, int H, int W, int32_t *labels, float *best,
                        cudaStream_t s, Profiler *prof);
 bool aggregate_supported(int n);
+bool aggregate_fits(const hgf_guidance *g);  // fused kernels take this shape
 
 }  // namespace hgf

@@ -7,7 +7,7 @@
 // the shift shrinks the cancellation in A(G_i G_j) - mu_i mu_j. Window sums are float32 direct
 // sums of 2r+1 terms per axis; the assembly Sigma = A(GG^T) - mu mu^T and the recursion run in the
 // precision chosen by hgf_params.inv_precision (float64 by default).
-#include "hgf_internal.cuh"
+#include "hgf_basis.cuh"
 
 #include <algorithm>
 
@@ -74,23 +74,41 @@ cudaError_t launch_make_guidance(const float *img, int C, int H, int W, const Ba
 constexpr int kMeanBlocks = 160;
 constexpr int kMeanThreads = 256;
 
-// partial[b * n + i] = sum of G_i over the pixels of block b's fixed range (float64, fixed order)
-__global__ void k_mean_partial(const float *__restrict__ G, int n, int HW,
-                               double *__restrict__ partial) {
-  __shared__ double red[kMeanThreads];
-  int per = (HW + gridDim.x - 1) / gridDim.x;
-  int p0 = blockIdx.x * per, p1 = min(HW, p0 + per);
-  for (int i = 0; i < n; ++i) {
+// partial[b * n + i] = sum of G_i over block b's fixed pixel range (float64, fixed order), with
+// G_i evaluated from the input image.
+template <int B>
+__global__ void __launch_bounds__(kMeanThreads) k_mean_partial(const float *__restrict__ img,
+                                                               int HW,
+                                                               double *__restrict__ partial) {
+  constexpr int N = basis_n(B), C = basis_channels_in(B);
+  __shared__ double red[kMeanThreads / 32][N];
+  const float zero[N] = {};
+  double acc[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) acc[i] = 0.0;
+  const int per = (HW + gridDim.x - 1) / gridDim.x;
+  const int p0 = blockIdx.x * per, p1 = min(HW, p0 + per);
+  for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+    float x[C], g[N];
+#pragma unroll
+    for (int c = 0; c < C; ++c) x[c] = __ldg(img + (size_t)c * HW + p);
+    eval_basis<B>(x, zero, g);
+#pragma unroll
+    for (int i = 0; i < N; ++i) acc[i] += g[i];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    double v = acc[i];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) red[warp][i] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < N) {
     double s = 0.0;
-    for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) s += G[(size_t)i * HW + p];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-      if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) partial[blockIdx.x * n + i] = red[0];
-    __syncthreads();
+    for (int w = 0; w < kMeanThreads / 32; ++w) s += red[w][threadIdx.x];
+    partial[blockIdx.x * N + threadIdx.x] = s;
   }
 }
 
@@ -103,11 +121,21 @@ __global__ void k_mean_final(const double *__restrict__ partial, int nblk, int n
   shift[i] = (float)(s / HW);
 }
 
-__global__ void k_apply_shift(float *__restrict__ G, const float *__restrict__ shift, int n,
-                              int HW) {
-  size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+// Shifted guidance planes G_i - c_i (used by the moment sums and the plain form).
+template <int B>
+__global__ void k_shifted_guidance(const float *__restrict__ img, const float *__restrict__ shift,
+                                   int HW, float *__restrict__ G) {
+  constexpr int N = basis_n(B), C = basis_channels_in(B);
+  const size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (p >= (size_t)HW) return;
-  for (int i = 0; i < n; ++i) G[(size_t)i * HW + p] -= shift[i];
+  float x[C], sh[N], g[N];
+#pragma unroll
+  for (int c = 0; c < C; ++c) x[c] = img[(size_t)c * HW + p];
+#pragma unroll
+  for (int i = 0; i < N; ++i) sh[i] = shift[i];
+  eval_basis<B>(x, sh, g);
+#pragma unroll
+  for (int i = 0; i < N; ++i) G[(size_t)i * HW + p] = g[i];
 }
 
 // ------------------------------------------------------------------------- moment row sums
@@ -145,9 +173,27 @@ __global__ void k_moment_rows(const float *__restrict__ G, int n, int H, int W, 
   rows[(size_t)m * HW + (size_t)y * W + x] = s;
 }
 
+// ------------------------------------------------------------------ moment column sums
+// mom[m][y][x] = sum over the clipped vertical window of rows[m][.][x]: the full window sums of
+// every moment channel (Prop. 2: the Gram entries are box sums).
+__global__ void k_moment_cols(const float *__restrict__ rows, int H, int W, int r,
+                              float *__restrict__ mom) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  const int m = blockIdx.z;
+  if (x >= W) return;
+  const size_t HW = (size_t)H * W;
+  const float *src = rows + (size_t)m * HW + x;
+  const int y0 = max(0, y - r), y1 = min(H - 1, y + r);
+  float s = 0.f;
+#pragma unroll 4
+  for (int yy = y0; yy <= y1; ++yy) s += __ldg(src + (size_t)yy * W);
+  mom[(size_t)m * HW + (size_t)y * W + x] = s;
+}
+
 // ------------------------------------------------------------------- assembly + HGF inverse
-// One thread per pixel. Column sums of the moment rows give the window sums; dividing by N gives
-// the means mu_i = A(G_i) and E_ij = A(G_i G_j). Then S = E - mu mu^T (Sec. 5.1) and Prop. 1 with
+// One thread per pixel. Dividing the window sums of the moments by N gives the means
+// mu_i = A(G_i) and E_ij = A(G_i G_j). Then S = E - mu mu^T (Sec. 5.1) and Prop. 1 with
 // lambda = eps: for kappa = 0..n-1 (starting from an empty alpha)
 //   u_i   = sum_{j<kappa} alpha_ij S_{j kappa}
 //   gamma = -1 / (1 + S_{kappa kappa} / lambda + sum_{i<kappa} S_{kappa i} u_i)
@@ -155,7 +201,7 @@ __global__ void k_moment_rows(const float *__restrict__ G, int n, int H, int W, 
 //   alpha_{kappa kappa} = gamma / lambda^2
 // which yields (lambda E + S)^-1 = lambda^-1 E + S alpha (Eq. HGF_w3) = -lambda alpha.
 template <int NG, typename T>
-__global__ void __launch_bounds__(128) k_inverse(const float *__restrict__ rows, int H, int W,
+__global__ void __launch_bounds__(128) k_inverse(const float *__restrict__ mom, int H, int W,
                                                  int r, double eps, int combine,
                                                  float *__restrict__ minv,
                                                  float *__restrict__ mu) {
@@ -165,27 +211,21 @@ __global__ void __launch_bounds__(128) k_inverse(const float *__restrict__ rows,
   if (x >= W) return;
   size_t HW = (size_t)H * W;
   size_t pix = (size_t)y * W + x;
-  int y0 = max(0, y - r), y1 = min(H - 1, y + r);
-  const T invN = T(1) / T(clipped_count(x, r, W) * (y1 - y0 + 1));
+  const T invN = T(1) / T(clipped_count(x, r, W) * clipped_count(y, r, H));
 
+  float raw[NG + P];
+#pragma unroll
+  for (int e = 0; e < NG + P; ++e) raw[e] = __ldg(mom + (size_t)e * HW + pix);
   T m[NG];
 #pragma unroll
-  for (int i = 0; i < NG; ++i) {
-    const float *src = rows + (size_t)i * HW + x;
-    float s = 0.f;
-    for (int yy = y0; yy <= y1; ++yy) s += __ldg(src + (size_t)yy * W);
-    m[i] = T(s) * invN;
-  }
+  for (int i = 0; i < NG; ++i) m[i] = T(raw[i]) * invN;
   T S[P];
 #pragma unroll
   for (int i = 0; i < NG; ++i) {
 #pragma unroll
     for (int j = i; j < NG; ++j) {
       const int e = tri_index(NG, i, j);
-      const float *src = rows + (size_t)(NG + e) * HW + x;
-      float s = 0.f;
-      for (int yy = y0; yy <= y1; ++yy) s += __ldg(src + (size_t)yy * W);
-      S[e] = T(s) * invN - m[i] * m[j];
+      S[e] = T(raw[NG + e]) * invN - m[i] * m[j];
     }
   }
 
@@ -241,21 +281,21 @@ __global__ void __launch_bounds__(128) k_inverse(const float *__restrict__ rows,
 }
 
 template <int NG, typename T>
-static void launch_inverse_t(const float *rows, const hgf_guidance *g, cudaStream_t s,
+static void launch_inverse_t(const float *mom, const hgf_guidance *g, cudaStream_t s,
                              Profiler *prof) {
   dim3 grid((g->W + 127) / 128, g->H);
   LaunchScope ls(prof, "k_inverse", s);
-  k_inverse<NG, T><<<grid, 128, 0, s>>>(rows, g->H, g->W, g->r, g->eps, g->combine, g->minv,
+  k_inverse<NG, T><<<grid, 128, 0, s>>>(mom, g->H, g->W, g->r, g->eps, g->combine, g->minv,
                                          g->mu);
 }
 
 template <typename T>
-static bool launch_inverse_n(const float *rows, const hgf_guidance *g, cudaStream_t s,
+static bool launch_inverse_n(const float *mom, const hgf_guidance *g, cudaStream_t s,
                              Profiler *prof) {
   switch (g->n) {
 #define HGF_INV_CASE(N) \
   case N:               \
-    launch_inverse_t<N, T>(rows, g, s, prof); \
+    launch_inverse_t<N, T>(mom, g, s, prof); \
     return true;
     HGF_INV_CASE(1) HGF_INV_CASE(2) HGF_INV_CASE(3) HGF_INV_CASE(4) HGF_INV_CASE(5)
     HGF_INV_CASE(6) HGF_INV_CASE(7) HGF_INV_CASE(8) HGF_INV_CASE(9) HGF_INV_CASE(19)
@@ -267,45 +307,53 @@ static bool launch_inverse_n(const float *rows, const hgf_guidance *g, cudaStrea
 
 size_t prepare_workspace_bytes(int n, int H, int W) {
   size_t M = (size_t)n + (size_t)n * (n + 1) / 2;
-  size_t rows = M * (size_t)H * W * sizeof(float);
+  size_t plane = ((M * (size_t)H * W * sizeof(float) + 255) / 256) * 256;
   size_t part = (size_t)kMeanBlocks * n * sizeof(double);
-  return ((rows + 255) / 256) * 256 + part;
+  return 2 * plane + part;  // row sums, window sums, mean partials
 }
 
 cudaError_t launch_prepare(hgf_guidance *g, const float *img, void *ws, size_t ws_size,
                            cudaStream_t s, Profiler *prof) {
-  BasisTable bt;
-  if (!make_basis_table(g->C, g->degree, g->basis, &bt) || bt.n != g->n)
-    return cudaErrorInvalidValue;
+  const int b = basis_id(g->C, g->degree, g->basis);
+  if (b < 0 || basis_n(b) != g->n) return cudaErrorInvalidValue;
   const int H = g->H, W = g->W, n = g->n, HW = H * W;
-  size_t M = (size_t)n + (size_t)n * (n + 1) / 2;
+  const size_t M = (size_t)n + (size_t)n * (n + 1) / 2;
   if (ws_size < prepare_workspace_bytes(n, H, W)) return cudaErrorInvalidValue;
+  const size_t plane = ((M * HW * sizeof(float) + 255) / 256) * 256;
   float *rows = (float *)ws;
-  double *partial = (double *)((char *)ws + ((M * HW * sizeof(float) + 255) / 256) * 256);
+  float *mom = (float *)((char *)ws + plane);
+  double *partial = (double *)((char *)ws + 2 * plane);
 
+  cudaError_t e = cudaMemcpyAsync(g->img, img, (size_t)g->C * HW * sizeof(float),
+                                  cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return e;
+  dispatch_basis(b, [&](auto bc) {
+    constexpr int B = decltype(bc)::value;
+    {
+      LaunchScope ls(prof, "k_mean_partial", s);
+      k_mean_partial<B><<<kMeanBlocks, kMeanThreads, 0, s>>>(g->img, HW, partial);
+    }
+    {
+      LaunchScope ls(prof, "k_mean_final", s);
+      k_mean_final<<<1, 32, 0, s>>>(partial, kMeanBlocks, n, HW, g->shift);
+    }
+    {
+      LaunchScope ls(prof, "k_shifted_guidance", s);
+      k_shifted_guidance<B><<<(HW + 255) / 256, 256, 0, s>>>(g->img, g->shift, HW, g->G);
+    }
+  });
   {
-    LaunchScope ls(prof, "k_make_guidance", s);
-    k_make_guidance<<<(HW + 255) / 256, 256, 0, s>>>(img, g->C, HW, bt, g->G);
-  }
-  {
-    LaunchScope ls(prof, "k_mean_partial", s);
-    k_mean_partial<<<kMeanBlocks, kMeanThreads, 0, s>>>(g->G, n, HW, partial);
-  }
-  {
-    LaunchScope ls(prof, "k_mean_final", s);
-    k_mean_final<<<1, 32, 0, s>>>(partial, kMeanBlocks, n, HW, g->shift);
-  }
-  {
-    LaunchScope ls(prof, "k_apply_shift", s);
-    k_apply_shift<<<(HW + 255) / 256, 256, 0, s>>>(g->G, g->shift, n, HW);
-  }
-  {
-    dim3 grid_rows((W + 127) / 128, H, (unsigned)M);
+    dim3 grid((W + 127) / 128, H, (unsigned)M);
     LaunchScope ls(prof, "k_moment_rows", s);
-    k_moment_rows<<<grid_rows, 128, 0, s>>>(g->G, n, H, W, g->r, rows);
+    k_moment_rows<<<grid, 128, 0, s>>>(g->G, n, H, W, g->r, rows);
   }
-  bool ok = g->inv_precision == HGF_F32 ? launch_inverse_n<float>(rows, g, s, prof)
-                                        : launch_inverse_n<double>(rows, g, s, prof);
+  {
+    dim3 grid((W + 127) / 128, H, (unsigned)M);
+    LaunchScope ls(prof, "k_moment_cols", s);
+    k_moment_cols<<<grid, 128, 0, s>>>(rows, H, W, g->r, mom);
+  }
+  bool ok = g->inv_precision == HGF_F32 ? launch_inverse_n<float>(mom, g, s, prof)
+                                        : launch_inverse_n<double>(mom, g, s, prof);
   if (!ok) return cudaErrorInvalidValue;
   return cudaGetLastError();
 }

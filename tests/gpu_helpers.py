@@ -60,12 +60,19 @@ def check_against_oracle(q, labels, best, ref, tol=TOL_Q, margin=MARGIN):
         assert np.all(np.isfinite(q)), "non-finite filtered values"
         assert err <= tol, f"normwise error {err:.3e} > {tol:.1e}"
     ol, ob, om = O.wta(ref)
+    scale = max(float(np.max(np.abs(ref))), 1e-30)
     sure = om > margin
     mism = (labels != ol) & sure
     assert not mism.any(), f"{mism.sum()} labels differ where the oracle margin > {margin}"
-    agree = float(np.mean(labels == ol))
-    assert agree >= MIN_AGREEMENT, f"label agreement {agree:.5f}"
-    assert np.max(np.abs(best - ob)) <= tol * max(np.max(np.abs(ref)), 1e-30) * 1.0001
+    # every GPU label is a minimum of the oracle's volume within the filtering tolerance
+    picked_ref = np.take_along_axis(ref, labels[None].astype(np.int64), axis=0)[0]
+    assert np.all(picked_ref - ob <= tol * scale), "a GPU label is not a minimum within tolerance"
+    # agreement over pixels whose oracle minimum is unique (exact ties, margin == 0 in float64,
+    # have several correct labels: e.g. labels l >= x at the left border see identical slices)
+    unique = om > 0
+    agree = float(np.mean(labels[unique] == ol[unique])) if unique.any() else 1.0
+    assert agree >= MIN_AGREEMENT, f"label agreement {agree:.5f} on {unique.sum()} unique pixels"
+    assert np.max(np.abs(best - ob)) <= tol * scale * 1.0001
     # labels must index a minimum of the GPU's own filtered volume where it was returned
     if q is not None:
         H, W = labels.shape
