@@ -139,13 +139,15 @@ hgf_status hgf_filter_host(hgf_ctx *ctx, const float *img, int C, int H, int W,
                            const hgf_params *params, const void *cost, int cost_dtype, int L,
                            int32_t *labels, float *best, void *stream);
 
-/* Tuning of the fused kernels (0 = automatic): labels per pass of the coefficient and output
- * kernels, row-band height, labels per chunk of the workspace. Returns HGF_EINVAL for values the
- * kernels cannot take. */
+/* Tuning of the fused kernels (0 = automatic): labels per pass of the coefficient kernel (2 or 4),
+ * row-band height, labels per chunk of the coefficient workspace, and how the output kernel gets
+ * the row leaving its vertical window (1 = shared-memory ring, 2 = reload from device memory).
+ * Returns HGF_EINVAL for values the kernels cannot take. */
 typedef struct {
   int labels_per_pass;
   int band_rows;
   int chunk_labels;
+  int apply_mode;
 } hgf_tuning;
 hgf_status hgf_set_tuning(hgf_ctx *ctx, const hgf_tuning *t);
 

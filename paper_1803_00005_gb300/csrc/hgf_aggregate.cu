@@ -117,8 +117,12 @@ __global__ void __launch_bounds__(NT) k_coef(const CT *__restrict__ cost, int H,
 #pragma unroll
     for (int c = 0; c < C1; ++c) V[k][c] = 0.f;
 
-  for (int s = s_begin; s < s_end; ++s) {
-    load_row(s + 2, pc);  // consumed two steps later
+  // One step per input row s: `cur` holds row s (loaded two steps earlier) and row s + 2 is
+  // loaded into `nxt`. The loop is unrolled three times so that the three buffers rotate roles
+  // without register copies (a copy would wait for the load it copies).
+  auto step = [&](const int s, const float *cur, float *nxt) {
+    if (s >= s_end) return;
+    load_row(s + 2, nxt);
     const int y1 = s - r;
     const int x = x0 + t;
     const bool coef_here = y1 >= Y0 && t < TW && x < W;
@@ -151,24 +155,19 @@ __global__ void __launch_bounds__(NT) k_coef(const CT *__restrict__ cost, int H,
       }
       if (s >= 0 && s < H) {
         float g[NG];
-        eval_basis<B>(pa, sh, g);
+        eval_basis<B>(cur, sh, g);
 #pragma unroll
-        for (int c = 0; c < RAW; ++c) slot[c * NT] = pa[c];
+        for (int c = 0; c < RAW; ++c) slot[c * NT] = cur[c];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-          const float p = pa[NC + k];
+          const float p = cur[NC + k];
           V[k][0] += p;
 #pragma unroll
           for (int i = 0; i < NG; ++i) V[k][i + 1] = fmaf(g[i], p, V[k][i + 1]);
         }
       }
     }
-#pragma unroll
-    for (int c = 0; c < RAW; ++c) {
-      pa[c] = pb[c];
-      pb[c] = pc[c];
-    }
-    if (y1 < Y0) continue;  // warm-up rows: no coefficient row complete yet (uniform per CTA)
+    if (y1 < Y0) return;  // warm-up rows: no coefficient row complete yet (uniform per CTA)
 
     // ---- phase B: horizontal window sums via inclusive prefix scans
 #pragma unroll
@@ -222,6 +221,11 @@ __global__ void __launch_bounds__(NT) k_coef(const CT *__restrict__ cost, int H,
       }
     }
     __syncthreads();
+  };
+  for (int s = s_begin; s < s_end; s += 3) {
+    step(s, pa, pc);
+    step(s + 1, pb, pa);
+    step(s + 2, pc, pb);
   }
 }
 
@@ -266,17 +270,30 @@ __global__ void __launch_bounds__(NT) k_apply(const float *__restrict__ coef, in
       for (int c = 0; c < C1; ++c) v[c] = __ldg(cb + (size_t)c * HW + pix);
     }
   };
+  // outgoing rows (only without the ring): row `row` if it entered this band's window
+  auto load_old = [&](int row, float *v) {
+    if (!RING && row >= add_lo) load_row(row, v);
+  };
   float pa[C1], pb[C1], pc[C1];
+  float oa[RING ? 1 : C1], ob[RING ? 1 : C1], oc[RING ? 1 : C1];
 #pragma unroll
   for (int c = 0; c < C1; ++c) pa[c] = pb[c] = pc[c] = 0.f;
+#pragma unroll
+  for (int c = 0; c < (RING ? 1 : C1); ++c) oa[c] = ob[c] = oc[c] = 0.f;
   load_row(s_begin, pa);
   load_row(s_begin + 1, pb);
+  load_old(s_begin - 2 * r - 1, oa);
+  load_old(s_begin + 1 - 2 * r - 1, ob);
   float V[C1];
 #pragma unroll
   for (int c = 0; c < C1; ++c) V[c] = 0.f;
 
-  for (int s = s_begin; s < s_end; ++s) {
-    load_row(s + 2, pc);
+  // Same three-buffer rotation as k_coef; without the ring, the outgoing row (2r+1 rows back,
+  // resident in L2) is prefetched two steps ahead as well.
+  auto step = [&](const int s, const float *cur, float *nxt, const float *cur_o, float *nxt_o) {
+    if (s >= s_end) return;
+    load_row(s + 2, nxt);
+    if (!RING) load_old(s + 2 - 2 * r - 1, nxt_o);
     const int y2 = s - r;
     const int x = x0 + t;
     const bool out_here = y2 >= Y0 && t < TW && x < W;
@@ -297,28 +314,22 @@ __global__ void __launch_bounds__(NT) k_apply(const float *__restrict__ coef, in
         if (s >= 0 && s < H) {
 #pragma unroll
           for (int c = 0; c < C1; ++c) {
-            V[c] += pa[c];
-            slot[c * NT] = pa[c];
+            V[c] += cur[c];
+            slot[c * NT] = cur[c];
           }
         }
       } else {
         if (so >= add_lo) {
-          const size_t pix = (size_t)so * W + xc;
 #pragma unroll
-          for (int c = 0; c < C1; ++c) V[c] -= __ldg(cb + (size_t)c * HW + pix);
+          for (int c = 0; c < C1; ++c) V[c] -= cur_o[c];
         }
         if (s >= 0 && s < H) {
 #pragma unroll
-          for (int c = 0; c < C1; ++c) V[c] += pa[c];
+          for (int c = 0; c < C1; ++c) V[c] += cur[c];
         }
       }
     }
-#pragma unroll
-    for (int c = 0; c < C1; ++c) {
-      pa[c] = pb[c];
-      pb[c] = pc[c];
-    }
-    if (y2 < Y0) continue;
+    if (y2 < Y0) return;
 
 #pragma unroll
     for (int c = 0; c < C1; ++c) sA[c * kRowStride + 4 + t] = V[c];
@@ -342,8 +353,14 @@ __global__ void __launch_bounds__(NT) k_apply(const float *__restrict__ coef, in
       if (keys) atomicMin(keys + pix, wta_key(q, label));
     }
     __syncthreads();
+  };
+  for (int s = s_begin; s < s_end; s += 3) {
+    step(s, pa, pc, oa, oc);
+    step(s + 1, pb, pa, ob, oa);
+    step(s + 2, pc, pb, oc, ob);
   }
 }
+
 
 __global__ void k_wta_finalize(const unsigned long long *__restrict__ keys, int HW,
                                int32_t *__restrict__ labels, float *__restrict__ best) {
@@ -382,7 +399,7 @@ cudaError_t set_smem(Kern k, size_t bytes) {
 template <int B, int K>
 cudaError_t launch_chunk(const hgf_guidance *g, const void *cost, int cost_dtype, int l_first,
                          int nc, float *filtered, float *coef_ws, unsigned long long *keys,
-                         int band_rows, cudaStream_t s, Profiler *prof) {
+                         int band_rows, bool apply_ring, cudaStream_t s, Profiler *prof) {
   const int H = g->H, W = g->W, r = g->r;
   const int TW = NT - 2 * r;
   const unsigned strips = (W + TW - 1) / TW, bands = (H + band_rows - 1) / band_rows;
@@ -408,7 +425,7 @@ cudaError_t launch_chunk(const hgf_guidance *g, const void *cost, int cost_dtype
     dim3 grid(strips, bands, nc);
     LaunchScope ls(prof, "k_apply", s);
     const size_t ring_sm = apply_smem_bytes<B, true>(r);
-    if (ring_sm <= 110 * 1024) {  // two CTAs per SM
+    if (apply_ring && ring_sm <= 227 * 1024) {
       e = set_smem(k_apply<B, true>, ring_sm);
       if (e != cudaSuccess) return e;
       k_apply<B, true><<<grid, NT, ring_sm, s>>>(coef_ws, H, W, r, g->img, g->shift, keys,
@@ -446,9 +463,8 @@ bool aggregate_fits(const hgf_guidance *g) {
 
 AggregatePlan plan_aggregate(const hgf_guidance *g, int L, const hgf_tuning &t, int num_sms) {
   AggregatePlan p;
-  // four labels per pass while two CTAs still fit on an SM, else two
-  const bool four_fits = g->n < 19 && coef_smem(g->n, g->C, 4, g->r) <= 113 * 1024;
-  p.K = four_fits ? 4 : 2;
+  // two labels per pass (measured faster than four: the four-label kernel runs out of registers)
+  p.K = 2;
   if (t.labels_per_pass == 2 || (t.labels_per_pass == 4 &&
                                  coef_smem(g->n, g->C, 4, g->r) <= 227 * 1024))
     p.K = t.labels_per_pass;
@@ -460,6 +476,10 @@ AggregatePlan plan_aggregate(const hgf_guidance *g, int L, const hgf_tuning &t, 
   const int TW = NT - 2 * g->r;
   const int strips = (g->W + TW - 1) / TW;
   const int passes = (p.chunk + p.K - 1) / p.K;
+  // the outgoing coefficient rows of the output kernel are reloaded by default: they were read
+  // 2r+1 steps earlier and are still in L2, and without the ring more CTAs fit on an SM
+  const size_t ring = sizeof(float) * (size_t)(g->n + 1) * ((2 * g->r + 1) * NT + kRowStride);
+  p.apply_ring = t.apply_mode == 1 && ring <= 227 * 1024;
   if (t.band_rows > 0) {
     p.band_rows = t.band_rows;
   } else {
@@ -496,11 +516,11 @@ cudaError_t launch_aggregate(const hgf_guidance *g, const void *cost, int cost_d
     for (int l0 = 0; l0 < L && e == cudaSuccess; l0 += p.chunk) {
       const int nc = std::min(p.chunk, L - l0);
       if (p.K == 4)
-        e = launch_chunk<B, 4>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, k, p.band_rows, s,
-                               prof);
+        e = launch_chunk<B, 4>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, k, p.band_rows,
+                               p.apply_ring, s, prof);
       else
-        e = launch_chunk<B, 2>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, k, p.band_rows, s,
-                               prof);
+        e = launch_chunk<B, 2>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, k, p.band_rows,
+                               p.apply_ring, s, prof);
     }
   });
   if (!ok) return cudaErrorInvalidValue;

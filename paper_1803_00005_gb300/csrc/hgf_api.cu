@@ -342,6 +342,8 @@ hgf_status hgf_set_tuning(hgf_ctx *ctx, const hgf_tuning *t) {
     return set_err(ctx, HGF_EINVAL, "labels_per_pass must be 0, 1, 2 or 4");
   if (t->band_rows < 0 || t->chunk_labels < 0)
     return set_err(ctx, HGF_EINVAL, "band_rows and chunk_labels must be >= 0");
+  if (t->apply_mode < 0 || t->apply_mode > 2)
+    return set_err(ctx, HGF_EINVAL, "apply_mode must be 0, 1 or 2");
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   ctx->tuning = *t;
   return HGF_OK;

@@ -137,7 +137,7 @@ struct hgf_ctx {
   hgf::Workspace ws_plain;       // plain-form intermediates
   hgf::Workspace ws_io;          // device copies for hgf_filter_host
   hgf_guidance *host_guidance = nullptr;  // reused by hgf_filter_host
-  hgf_tuning tuning{0, 0, 0};
+  hgf_tuning tuning{0, 0, 0, 0};
   int num_sms = 0;
   hgf::Profiler prof;
 };
@@ -168,6 +168,7 @@ struct AggregatePlan {
   int K;            // labels per pass
   int band_rows;    // coefficient/output rows per CTA band
   int chunk;        // labels per workspace chunk
+  bool apply_ring;  // output kernel keeps the outgoing rows in a shared-memory ring
 };
 AggregatePlan plan_aggregate(const hgf_guidance *g, int L, const hgf_tuning &t, int num_sms);
 size_t aggregate_coef_bytes(const hgf_guidance *g, const AggregatePlan &p);

@@ -48,7 +48,7 @@ class hgf_params(ctypes.Structure):
 
 class hgf_tuning(ctypes.Structure):
     _fields_ = [("labels_per_pass", ctypes.c_int), ("band_rows", ctypes.c_int),
-                ("chunk_labels", ctypes.c_int)]
+                ("chunk_labels", ctypes.c_int), ("apply_mode", ctypes.c_int)]
 
 
 _lib = None
@@ -236,9 +236,9 @@ def hgf_filter_host(ctx, img, cost, cost_dtype, params, labels, best=None, strea
     _check(ctx, st)
 
 
-def hgf_set_tuning(ctx, labels_per_pass=0, band_rows=0, chunk_labels=0):
+def hgf_set_tuning(ctx, labels_per_pass=0, band_rows=0, chunk_labels=0, apply_mode=0):
     t = hgf_tuning(labels_per_pass=labels_per_pass, band_rows=band_rows,
-                   chunk_labels=chunk_labels)
+                   chunk_labels=chunk_labels, apply_mode=apply_mode)
     _check(ctx, lib().hgf_set_tuning(ctx, ctypes.byref(t)))
 
 
