@@ -119,6 +119,23 @@ hgf_status hgf_aggregate(hgf_ctx *ctx, const hgf_guidance *g, const void *cost, 
                          int L, void *filtered, int filtered_dtype, int32_t *labels, float *best,
                          void *stream);
 
+/* hgf_aggregate for callers that cannot allocate device memory while they run (work recorded into
+ * a CUDA graph, fixed-latency loops, or programs whose device memory is handed out by their own
+ * allocator at start-up): the same kernels and results, but the scratch - per-pixel WTA keys and
+ * per-chunk coefficient planes - comes from one fixed 64 MiB file-scope device array instead of
+ * the context's growable workspace. No cudaMalloc/cudaFree or allocating library call is made.
+ * The paper has no counterpart; it is a property of this library only.
+ * The array is held by every GPU that loads the library until the process exits. The first call
+ * on a device looks up its address (cudaGetSymbolAddress) with that device current: make it before
+ * any stream capture. All calls share the array and it keeps the last call's contents (the keys
+ * are reset by every call); calls that overlap on the GPU race and must be serialised. Returns
+ * HGF_EUNSUPPORTED when one label's coefficient planes plus the keys exceed 64 MiB (about 1.3
+ * Mpixel at n = 9), or when the window is too wide for the fused kernels. Same arguments as
+ * hgf_aggregate. */
+hgf_status hgf_aggregate_static(hgf_ctx *ctx, const hgf_guidance *g, const void *cost,
+                                int cost_dtype, int L, void *filtered, int filtered_dtype,
+                                int32_t *labels, float *best, void *stream);
+
 /* The same computation as hgf_aggregate by the plain form: one kernel per step (products, row
  * sums, column sums, coefficients, row sums, column sums, output, WTA) with every intermediate
  * plane in device memory. Comparison baseline for the fused path. Same arguments. */

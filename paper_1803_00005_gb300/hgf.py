@@ -30,6 +30,7 @@ EXPORTED = [
     "hgf_prepare", "hgf_guidance_release", "hgf_guidance_info", "hgf_guidance_export",
     "hgf_aggregate", "hgf_aggregate_plain", "hgf_wta", "hgf_filter_host", "hgf_set_tuning",
     "hgf_guidance_update", "hgf_launch_count", "hgf_profile_enable", "hgf_profile_report",
+    "hgf_aggregate_static",
 ]
 
 
@@ -78,6 +79,7 @@ def lib():
         "hgf_guidance_export": (c_int, [vp, vp, vp, vp, vp]),
         "hgf_aggregate": (c_int, [vp, vp, vp, c_int, c_int, vp, c_int, vp, vp, vp]),
         "hgf_aggregate_plain": (c_int, [vp, vp, vp, c_int, c_int, vp, c_int, vp, vp, vp]),
+        "hgf_aggregate_static": (c_int, [vp, vp, vp, c_int, c_int, vp, c_int, vp, vp, vp]),
         "hgf_wta": (c_int, [vp, vp, c_int, c_int, c_int, c_int, vp, vp, vp]),
         "hgf_filter_host": (c_int, [vp, vp, c_int, c_int, c_int, P(hgf_params), vp, c_int, c_int,
                                     vp, vp, vp]),
@@ -198,6 +200,17 @@ def hgf_aggregate(ctx, g, cost, filtered=None, labels=None, best=None, stream=No
     L = cost.shape[0]
     _check(ctx, lib().hgf_aggregate(ctx, g, _ptr(cost), _dtype_code(cost), L, _ptr(filtered),
                                     HGF_F32, _ptr(labels), _ptr(best), _stream(stream)))
+
+
+def hgf_aggregate_static(ctx, g, cost, filtered=None, labels=None, best=None, stream=None):
+    """hgf_aggregate without device allocation: scratch comes from the library's fixed 64 MiB
+    device array (see include/hgf.h)."""
+    for t, nm in ((cost, "cost"), (filtered, "filtered"), (labels, "labels"), (best, "best")):
+        _require_cuda(t, nm)
+    L = cost.shape[0]
+    _check(ctx, lib().hgf_aggregate_static(ctx, g, _ptr(cost), _dtype_code(cost), L,
+                                           _ptr(filtered), HGF_F32, _ptr(labels), _ptr(best),
+                                           _stream(stream)))
 
 
 def hgf_aggregate_plain(ctx, g, cost, filtered=None, labels=None, best=None, stream=None):
