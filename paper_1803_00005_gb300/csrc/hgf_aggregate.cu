@@ -65,13 +65,13 @@ template <int B, int K, typename CT>
 __global__ void __launch_bounds__(NT) k_coef(const CT *__restrict__ cost, int H, int W, int r,
                                              const float *__restrict__ img,
                                              const float *__restrict__ shift,
-                                             const float *__restrict__ minv,
-                                             const float *__restrict__ mu,
+                                             const float *__restrict__ rec,
                                              float *__restrict__ coef, int l_first, int n_chunk,
                                              int band_rows) {
   constexpr int NG = basis_n(B), C1 = NG + 1, NC = basis_channels_in(B), RAW = NC + K;
   constexpr int P = NG * (NG + 1) / 2;
-  constexpr bool EARLY = P <= 64;  // the inverse fits in registers: load it ahead of the scans
+  constexpr int REC = record_floats(NG), CP = coef_floats(NG);
+  constexpr bool EARLY = REC <= 68;  // the record fits in registers: load it ahead of the scans
   extern __shared__ __align__(16) float smem[];
   float *sA = smem;
   float *ring = smem + K * C1 * kRowStride;  // [2r+1][RAW][NT], thread-private columns
@@ -126,14 +126,18 @@ __global__ void __launch_bounds__(NT) k_coef(const CT *__restrict__ cost, int H,
     const int y1 = s - r;
     const int x = x0 + t;
     const bool coef_here = y1 >= Y0 && t < TW && x < W;
-    float Mreg[EARLY ? P : 1], m[NG];
-    if (coef_here) {  // issued now, used after the scans: the latency overlaps phases A and B
-      const size_t pix = (size_t)y1 * W + x;
+    // per-pixel record [mu | packed Minv]: issued now, used after the scans so that the load
+    // latency overlaps phases A and B (when it fits in registers)
+    float Rg[EARLY ? REC : 4];
+    const float4 *rp = reinterpret_cast<const float4 *>(rec + ((size_t)y1 * W + x) * REC);
+    if (coef_here && EARLY) {
 #pragma unroll
-      for (int i = 0; i < NG; ++i) m[i] = __ldg(mu + (size_t)i * HW + pix);
-      if (EARLY) {
-#pragma unroll
-        for (int e = 0; e < (EARLY ? P : 1); ++e) Mreg[e] = __ldg(minv + (size_t)e * HW + pix);
+      for (int q = 0; q < (EARLY ? REC : 4) / 4; ++q) {
+        const float4 v = __ldg(rp + q);
+        Rg[4 * q] = v.x;
+        Rg[4 * q + 1] = v.y;
+        Rg[4 * q + 2] = v.z;
+        Rg[4 * q + 3] = v.w;
       }
     }
     // ---- phase A: vertical running sums over input rows [s-2r, s]
@@ -182,6 +186,12 @@ __global__ void __launch_bounds__(NT) k_coef(const CT *__restrict__ cost, int H,
     if (coef_here) {
       const size_t pix = (size_t)y1 * W + x;
       const float invN = 1.f / (float)(clipped_count(x, r, W) * clipped_count(y1, r, H));
+      auto recv = [&](int e) -> float {
+        return EARLY ? Rg[EARLY ? e : 0] : __ldg(rec + pix * REC + e);
+      };
+      float m[NG];
+#pragma unroll
+      for (int i = 0; i < NG; ++i) m[i] = recv(i);
       float cov[K][NG], a[K][NG], pbar[K];
 #pragma unroll
       for (int k = 0; k < K; ++k) {
@@ -198,8 +208,7 @@ __global__ void __launch_bounds__(NT) k_coef(const CT *__restrict__ cost, int H,
       for (int i = 0; i < NG; ++i) {
 #pragma unroll
         for (int j = i; j < NG; ++j) {
-          const float Mij = EARLY ? Mreg[EARLY ? tri_index(NG, i, j) : 0]
-                                  : __ldg(minv + (size_t)tri_index(NG, i, j) * HW + pix);
+          const float Mij = recv(NG + tri_index(NG, i, j));
 #pragma unroll
           for (int k = 0; k < K; ++k) {
             a[k][i] = fmaf(Mij, cov[k][j], a[k][i]);
@@ -213,10 +222,15 @@ __global__ void __launch_bounds__(NT) k_coef(const CT *__restrict__ cost, int H,
           float b = pbar[k];
 #pragma unroll
           for (int i = 0; i < NG; ++i) b = fmaf(-a[k][i], m[i], b);
-          float *dst = coef + (size_t)(k0 + k) * C1 * HW + pix;
-          dst[0] = b;
+          float o[CP];
+          o[0] = b;
 #pragma unroll
-          for (int i = 0; i < NG; ++i) dst[(size_t)(i + 1) * HW] = a[k][i];
+          for (int i = 0; i < NG; ++i) o[i + 1] = a[k][i];
+#pragma unroll
+          for (int i = C1; i < CP; ++i) o[i] = 0.f;
+          float2 *dst = reinterpret_cast<float2 *>(coef + ((size_t)(k0 + k) * HW + pix) * CP);
+#pragma unroll
+          for (int q = 0; q < CP / 2; ++q) dst[q] = make_float2(o[2 * q], o[2 * q + 1]);
         }
       }
     }
@@ -244,7 +258,7 @@ __global__ void __launch_bounds__(NT) k_apply(const float *__restrict__ coef, in
                                               unsigned long long *__restrict__ keys,
                                               float *__restrict__ filtered, int l_first,
                                               int band_rows) {
-  constexpr int NG = basis_n(B), C1 = NG + 1, NC = basis_channels_in(B);
+  constexpr int NG = basis_n(B), C1 = NG + 1, NC = basis_channels_in(B), CP = coef_floats(NG);
   extern __shared__ __align__(16) float smem[];
   float *sA = smem;
   float *ring = smem + C1 * kRowStride;  // [2r+1][C1][NT]
@@ -262,12 +276,19 @@ __global__ void __launch_bounds__(NT) k_apply(const float *__restrict__ coef, in
   const int s_begin = Y0 - r, s_end = Y1 + r;
 
   if (t < C1) sA[t * kRowStride + 3] = 0.f;
-  const float *cb = coef + (size_t)k * C1 * HW;
+  float sh[NG];
+#pragma unroll
+  for (int i = 0; i < NG; ++i) sh[i] = __ldg(shift + i);
+  const float *cb = coef + (size_t)k * HW * CP;
   auto load_row = [&](int row, float *v) {
     if (col_ok && row >= 0 && row < H) {
-      const size_t pix = (size_t)row * W + xc;
+      const float2 *src = reinterpret_cast<const float2 *>(cb + ((size_t)row * W + xc) * CP);
 #pragma unroll
-      for (int c = 0; c < C1; ++c) v[c] = __ldg(cb + (size_t)c * HW + pix);
+      for (int q = 0; q < CP / 2; ++q) {
+        const float2 u = __ldg(src + q);
+        if (2 * q < C1) v[2 * q] = u.x;
+        if (2 * q + 1 < C1) v[2 * q + 1] = u.y;
+      }
     }
   };
   // outgoing rows (only without the ring): row `row` if it entered this band's window
@@ -340,9 +361,7 @@ __global__ void __launch_bounds__(NT) k_apply(const float *__restrict__ coef, in
     if (out_here) {
       const size_t pix = (size_t)y2 * W + x;
       const float invN = 1.f / (float)(clipped_count(x, r, W) * clipped_count(y2, r, H));
-      float sh[NG], g[NG];
-#pragma unroll
-      for (int i = 0; i < NG; ++i) sh[i] = __ldg(shift + i);
+      float g[NG];
       eval_basis<B>(xin, sh, g);
       float q = window(sA, t, r);
 #pragma unroll
@@ -396,23 +415,57 @@ cudaError_t set_smem(Kern k, size_t bytes) {
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// Rows per band for a kernel whose grid is strips x bands x slabs: the band count that minimises
+// (waves of resident CTAs) x (rows streamed per CTA, including the 2r warm-up rows).
+static int choose_band_rows(int H, int r, long long strips_slabs, int resident) {
+  long long best_cost = -1;
+  int best = H;
+  for (int bands = 1; bands <= std::max(1, H / std::max(8, 2 * r)); ++bands) {
+    const int rows = (H + bands - 1) / bands;
+    const long long ctas = strips_slabs * ((H + rows - 1) / rows);
+    const long long waves = (ctas + resident - 1) / resident;
+    const long long cost = waves * (rows + 2 * r);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = rows;
+    }
+  }
+  return best;
+}
+
+template <typename Kern>
+static int resident_ctas(Kern k, size_t smem) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem) != cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  return std::max(1, per_sm) * std::max(1, sms);
+}
+
 template <int B, int K>
 cudaError_t launch_chunk(const hgf_guidance *g, const void *cost, int cost_dtype, int l_first,
                          int nc, float *filtered, float *coef_ws, unsigned long long *keys,
                          int band_rows, bool apply_ring, cudaStream_t s, Profiler *prof) {
   const int H = g->H, W = g->W, r = g->r;
   const int TW = NT - 2 * r;
-  const unsigned strips = (W + TW - 1) / TW, bands = (H + band_rows - 1) / band_rows;
+  const unsigned strips = (W + TW - 1) / TW;
   cudaError_t e;
   {
-    dim3 grid(strips, bands, (nc + K - 1) / K);
     const size_t sm = coef_smem_bytes<B, K>(r);
+    const int passes = (nc + K - 1) / K;
+    const int rows = band_rows > 0 ? band_rows
+                                   : choose_band_rows(H, r, (long long)strips * passes,
+                                                      resident_ctas(k_coef<B, K, float>, sm));
+    dim3 grid(strips, (H + rows - 1) / rows, passes);
     LaunchScope ls(prof, "k_coef", s);
 #define HGF_COEF(CT)                                                                          \
   e = set_smem(k_coef<B, K, CT>, sm);                                                         \
   if (e != cudaSuccess) return e;                                                             \
-  k_coef<B, K, CT><<<grid, NT, sm, s>>>((const CT *)cost, H, W, r, g->img, g->shift, g->minv, \
-                                        g->mu, coef_ws, l_first, nc, band_rows);
+  k_coef<B, K, CT><<<grid, NT, sm, s>>>((const CT *)cost, H, W, r, g->img, g->shift, g->rec,  \
+                                        coef_ws, l_first, nc, rows);
     switch (cost_dtype) {
       case HGF_F32: HGF_COEF(float) break;
       case HGF_BF16: HGF_COEF(__nv_bfloat16) break;
@@ -422,20 +475,27 @@ cudaError_t launch_chunk(const hgf_guidance *g, const void *cost, int cost_dtype
 #undef HGF_COEF
   }
   {
-    dim3 grid(strips, bands, nc);
     LaunchScope ls(prof, "k_apply", s);
     const size_t ring_sm = apply_smem_bytes<B, true>(r);
     if (apply_ring && ring_sm <= 227 * 1024) {
+      const int rows = band_rows > 0 ? band_rows
+                                     : choose_band_rows(H, r, (long long)strips * nc,
+                                                        resident_ctas(k_apply<B, true>, ring_sm));
+      dim3 grid(strips, (H + rows - 1) / rows, nc);
       e = set_smem(k_apply<B, true>, ring_sm);
       if (e != cudaSuccess) return e;
       k_apply<B, true><<<grid, NT, ring_sm, s>>>(coef_ws, H, W, r, g->img, g->shift, keys,
-                                                 filtered, l_first, band_rows);
+                                                 filtered, l_first, rows);
     } else {
       const size_t sm = apply_smem_bytes<B, false>(r);
+      const int rows = band_rows > 0 ? band_rows
+                                     : choose_band_rows(H, r, (long long)strips * nc,
+                                                        resident_ctas(k_apply<B, false>, sm));
+      dim3 grid(strips, (H + rows - 1) / rows, nc);
       e = set_smem(k_apply<B, false>, sm);
       if (e != cudaSuccess) return e;
       k_apply<B, false><<<grid, NT, sm, s>>>(coef_ws, H, W, r, g->img, g->shift, keys, filtered,
-                                             l_first, band_rows);
+                                             l_first, rows);
     }
   }
   return cudaGetLastError();
@@ -468,7 +528,7 @@ AggregatePlan plan_aggregate(const hgf_guidance *g, int L, const hgf_tuning &t, 
   if (t.labels_per_pass == 2 || (t.labels_per_pass == 4 &&
                                  coef_smem(g->n, g->C, 4, g->r) <= 227 * 1024))
     p.K = t.labels_per_pass;
-  const size_t plane = (size_t)(g->n + 1) * g->H * g->W * sizeof(float);
+  const size_t plane = (size_t)coef_floats(g->n) * g->H * g->W * sizeof(float);
   // labels per chunk: all labels while the coefficient workspace stays under 4 GiB
   size_t cap = std::max<size_t>(1, ((size_t)4 << 30) / plane);
   p.chunk = t.chunk_labels > 0 ? t.chunk_labels : (int)std::min<size_t>((size_t)L, cap);
@@ -480,21 +540,15 @@ AggregatePlan plan_aggregate(const hgf_guidance *g, int L, const hgf_tuning &t, 
   // 2r+1 steps earlier and are still in L2, and without the ring more CTAs fit on an SM
   const size_t ring = sizeof(float) * (size_t)(g->n + 1) * ((2 * g->r + 1) * NT + kRowStride);
   p.apply_ring = t.apply_mode == 1 && ring <= 227 * 1024;
-  if (t.band_rows > 0) {
-    p.band_rows = t.band_rows;
-  } else {
-    // about 2 CTAs per SM for the coefficient kernel, with bands of at least 4r rows so the
-    // warm-up rows stay a fraction of the work
-    const int target = 2 * std::max(1, num_sms);
-    int bands = std::max(1, (target + strips * passes - 1) / (strips * passes));
-    int rows = (g->H + bands - 1) / bands;
-    p.band_rows = std::max(rows, std::min(g->H, std::max(16, 4 * g->r)));
-  }
+  (void)strips;
+  (void)passes;
+  (void)num_sms;
+  p.band_rows = t.band_rows;  // 0: each kernel picks its bands from its occupancy at launch
   return p;
 }
 
 size_t aggregate_coef_bytes(const hgf_guidance *g, const AggregatePlan &p) {
-  return (size_t)p.chunk * (g->n + 1) * g->H * g->W * sizeof(float);
+  return (size_t)p.chunk * coef_floats(g->n) * g->H * g->W * sizeof(float);
 }
 
 cudaError_t launch_aggregate(const hgf_guidance *g, const void *cost, int cost_dtype, int L,

@@ -130,7 +130,7 @@ hgf_status alloc_guidance(hgf_ctx *ctx, int C, int H, int W, int n, const hgf_pa
   g->inv_precision = p->inv_precision;
   g->combine = p->combine;
   const size_t HW = (size_t)H * W;
-  const size_t floats = HW * ((size_t)C + n + packed_size(n) + n) + 64;
+  const size_t floats = HW * ((size_t)C + n + packed_size(n) + n + record_floats(n)) + 64;
   float *base = nullptr;
   cudaError_t e = cudaMalloc(&base, floats * sizeof(float));
   if (e != cudaSuccess) {
@@ -139,7 +139,8 @@ hgf_status alloc_guidance(hgf_ctx *ctx, int C, int H, int W, int n, const hgf_pa
     return set_err(ctx, HGF_ENOMEM, "cannot allocate %zu bytes for the guidance",
                    floats * sizeof(float));
   }
-  g->img = base;
+  g->rec = base;  // first: float4 records need the allocation's alignment
+  g->img = g->rec + (size_t)record_floats(n) * HW;
   g->G = g->img + (size_t)C * HW;
   g->minv = g->G + (size_t)n * HW;
   g->mu = g->minv + (size_t)packed_size(n) * HW;
@@ -244,7 +245,7 @@ hgf_status hgf_destroy(hgf_ctx *ctx) {
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
   if (ctx->host_guidance) {
-    cudaFree(ctx->host_guidance->img);
+    cudaFree(ctx->host_guidance->rec);
     delete ctx->host_guidance;
   }
   for (auto &rec : ctx->prof.recs) {
@@ -297,7 +298,7 @@ hgf_status hgf_prepare(hgf_ctx *ctx, const float *img, int C, int H, int W,
     st = prepare_locked(ctx, g, img, (cudaStream_t)stream);
   }
   if (st != HGF_OK) {
-    cudaFree(g->img);
+    cudaFree(g->rec);
     delete g;
     return st;
   }
@@ -308,7 +309,7 @@ hgf_status hgf_prepare(hgf_ctx *ctx, const float *img, int C, int H, int W,
 hgf_status hgf_guidance_release(hgf_guidance *g) {
   if (!g) return HGF_OK;
   cudaSetDevice(g->ctx->device);
-  cudaFree(g->img);
+  cudaFree(g->rec);
   delete g;
   return HGF_OK;
 }
@@ -428,7 +429,7 @@ hgf_status hgf_filter_host(hgf_ctx *ctx, const float *img, int C, int H, int W,
   if (!same_shape(ctx->host_guidance, C, H, W, params)) {
     if (ctx->host_guidance) {
       cudaStreamSynchronize(s);
-      cudaFree(ctx->host_guidance->img);
+      cudaFree(ctx->host_guidance->rec);
       delete ctx->host_guidance;
       ctx->host_guidance = nullptr;
     }

@@ -31,6 +31,15 @@ bool make_basis_table(int C, int degree, int basis, BasisTable *t);
 
 inline int packed_size(int n) { return n * (n + 1) / 2; }
 
+// Per-pixel record of the resident inverse used by the fused kernels: [mu_0..mu_{n-1} |
+// packed Minv | padding], a multiple of 4 floats so that records are 16-byte aligned.
+__host__ __device__ constexpr int record_floats(int n) {
+  return (n + n * (n + 1) / 2 + 3) / 4 * 4;
+}
+// Per-pixel coefficient record of the fused kernels' workspace: [b, a_1..a_n | padding] rounded
+// up to an even count so that it is read and written as float2 pairs.
+__host__ __device__ constexpr int coef_floats(int n) { return (n + 1 + 1) / 2 * 2; }
+
 // Packed upper-triangle index of (i, j), i <= j, row by row.
 __host__ __device__ constexpr int tri_index(int n, int i, int j) {
   return i * n - (i * (i - 1)) / 2 + (j - i);
@@ -151,6 +160,7 @@ struct hgf_guidance {
   float *G = nullptr;      // n x H x W, shifted guidance G_i - c_i
   float *minv = nullptr;   // n(n+1)/2 x H x W, packed (Sigma + eps E)^-1
   float *mu = nullptr;     // n x H x W, shifted means A(G_i) - c_i
+  float *rec = nullptr;    // H x W x record_floats(n): [mu | packed Minv] per pixel
   float *shift = nullptr;  // n, device: c_i (image mean of G_i)
 };
 
@@ -166,7 +176,7 @@ cudaError_t launch_export(const hgf_guidance *g, float *minv_out, float *mu_out,
 
 struct AggregatePlan {
   int K;            // labels per pass
-  int band_rows;    // coefficient/output rows per CTA band
+  int band_rows;    // coefficient/output rows per CTA band (0: chosen per kernel from occupancy)
   int chunk;        // labels per workspace chunk
   bool apply_ring;  // output kernel keeps the outgoing rows in a shared-memory ring
 };

@@ -204,7 +204,8 @@ template <int NG, typename T>
 __global__ void __launch_bounds__(128) k_inverse(const float *__restrict__ mom, int H, int W,
                                                  int r, double eps, int combine,
                                                  float *__restrict__ minv,
-                                                 float *__restrict__ mu) {
+                                                 float *__restrict__ mu,
+                                                 float *__restrict__ rec) {
   constexpr int P = NG * (NG + 1) / 2;
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   int y = blockIdx.y;
@@ -259,6 +260,10 @@ __global__ void __launch_bounds__(128) k_inverse(const float *__restrict__ mom, 
     al[tri_index(NG, k, k)] = gam * inv_lam * inv_lam;
   }
 
+  constexpr int REC = record_floats(NG);
+  float out[REC];
+#pragma unroll
+  for (int i = 0; i < NG; ++i) out[i] = (float)m[i];
   if (combine == HGF_COMBINE_W3) {
 #pragma unroll
     for (int i = 0; i < NG; ++i) {
@@ -269,15 +274,23 @@ __global__ void __launch_bounds__(128) k_inverse(const float *__restrict__ mom, 
         for (int k = 0; k < NG; ++k)
           acc = fma(S[tri_index(NG, i < k ? i : k, i < k ? k : i)],
                     al[tri_index(NG, k < j ? k : j, k < j ? j : k)], acc);
-        minv[(size_t)tri_index(NG, i, j) * HW + pix] = (float)acc;
+        out[NG + tri_index(NG, i, j)] = (float)acc;
       }
     }
   } else {
 #pragma unroll
-    for (int e = 0; e < P; ++e) minv[(size_t)e * HW + pix] = (float)(-lam * al[e]);
+    for (int e = 0; e < P; ++e) out[NG + e] = (float)(-lam * al[e]);
   }
 #pragma unroll
-  for (int i = 0; i < NG; ++i) mu[(size_t)i * HW + pix] = (float)m[i];
+  for (int e = NG + P; e < REC; ++e) out[e] = 0.f;
+#pragma unroll
+  for (int e = 0; e < P; ++e) minv[(size_t)e * HW + pix] = out[NG + e];
+#pragma unroll
+  for (int i = 0; i < NG; ++i) mu[(size_t)i * HW + pix] = out[i];
+  float4 *dst = reinterpret_cast<float4 *>(rec + pix * REC);
+#pragma unroll
+  for (int q = 0; q < REC / 4; ++q)
+    dst[q] = make_float4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
 }
 
 template <int NG, typename T>
@@ -286,7 +299,7 @@ static void launch_inverse_t(const float *mom, const hgf_guidance *g, cudaStream
   dim3 grid((g->W + 127) / 128, g->H);
   LaunchScope ls(prof, "k_inverse", s);
   k_inverse<NG, T><<<grid, 128, 0, s>>>(mom, g->H, g->W, g->r, g->eps, g->combine, g->minv,
-                                         g->mu);
+                                         g->mu, g->rec);
 }
 
 template <typename T>
