@@ -64,7 +64,71 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-crop", type=int, nargs=2, default=(225, 188),
                     help="width height of the centred crop the CPU baseline runs on")
+    ap.add_argument("--serve", action="store_true",
+                    help="open-loop serving run (Poisson arrivals) instead of the step benchmark")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: mean requests per second")
+    ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals")
+    ap.add_argument("--warm", type=float, default=2.0, help="serving: seconds before measuring")
+    ap.add_argument("--slots", type=int, default=4)
     return ap.parse_args()
+
+
+def serve_arm(args):
+    """Open-loop serving: requests arrive at Poisson times (synth.serving_requests: sizes
+    640x480 .. 1920x1080, L 64..256, degree 1..3, r in {4, 9}, bf16 costs, 30% reuse an earlier
+    guidance) and are submitted to hgf_serve at their arrival time; latency counts from the
+    scheduled arrival. Inputs come from a pool of device-resident stereo pairs per size (costs
+    built on the device before the clock starts)."""
+    import numpy as np
+    import torch
+    from paper_1803_00005_gb300 import build, hgf, synth
+    build.build()
+    torch.cuda.set_device(0)
+    n_req = int(args.rate * (args.duration + args.warm)) + 1
+    reqs = synth.serving_requests(n_req, rate_hz=args.rate, seed=5)
+    pool = {}
+    for sp in reqs:
+        key = (sp["width"], sp["height"])
+        if key not in pool:
+            left, right, _ = synth.stereo_pair(sp["width"], sp["height"], 256, 5000 + len(pool))
+            pool[key] = dict(img=torch.from_numpy(left.astype(np.float32)).cuda(),
+                             cost=synth.cost_volume_torch(left, right, 256, "bf16"),
+                             labels=torch.empty((sp["height"], sp["width"]), dtype=torch.int32,
+                                                device="cuda"))
+    torch.cuda.synchronize()
+    srv = hgf.hgf_serve_create(0, budget_bytes=120 << 30, slots=args.slots, max_queue=4096,
+                               max_pixels=1920 * 1080, max_n=19)
+    t0 = time.perf_counter() + 0.5
+    ids, measured = [], []
+    warm_end = None
+    for i, sp in enumerate(reqs):
+        p = pool[(sp["width"], sp["height"])]
+        params = hgf.make_params(degree=sp["degree"], r=sp["r"], eps=sp["eps"])
+        cost = p["cost"][:sp["n_labels"]]
+        req = hgf.make_request(sp["guidance_key"], p["img"], cost, params, p["labels"])
+        now = time.perf_counter()
+        wait = t0 + sp["arrival_s"] - now
+        if wait > 0:
+            time.sleep(wait)
+        if warm_end is None and sp["arrival_s"] >= args.warm:
+            hgf.hgf_serve_stats(srv, reset=True)
+            warm_end = i
+        st, rid = hgf.hgf_serve_submit(srv, req)
+        ids.append((st, rid))
+    for st, rid in ids:
+        if st == hgf.HGF_OK:
+            hgf.hgf_serve_wait(srv, rid, 600000)
+    stats = hgf.hgf_serve_stats(srv)
+    hgf.hgf_serve_destroy(srv)
+    line = dict(metric="served HGF aggregate+WTA: p50/p99 latency and throughput",
+                value=stats["mpixel_labels_per_s"], unit=UNIT, n_gpus=1,
+                higher_is_better=True, impl="serve", data="synthetic",
+                config=dict(workload=f"Poisson {args.rate:g} req/s for {args.duration:g} s after "
+                                     f"{args.warm:g} s warm-up; 640x480..1920x1080, L 64..256, "
+                                     f"n in {{3, 9, 19}}, r in {{4, 9}}, bf16 costs, 30% guidance "
+                                     f"reuse, 120 GiB budget, {args.slots} slots"),
+                serve=stats)
+    print(json.dumps(line), flush=True)
 
 
 # ------------------------------------------------------------------------------ CPU oracle arm
@@ -176,6 +240,8 @@ class ClockSampler:
 def main():
     args = parse()
     w = WORKLOADS[args.workload]
+    if args.serve:
+        return serve_arm(args)
     if args.impl == "reference":
         return reference_arm(args, w)
 

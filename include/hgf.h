@@ -168,6 +168,61 @@ typedef struct {
 } hgf_tuning;
 hgf_status hgf_set_tuning(hgf_ctx *ctx, const hgf_tuning *t);
 
+/* ---------------------------------------------------------------------------------------------
+ * Serving (no counterpart in the paper): a request loop in a background thread that admits
+ * multi-label jobs of different sizes, label counts and guidance degrees against a device-memory
+ * budget, keeps each guidance's resident inverse (hgf_prepare) in an LRU cache shared by
+ * requests with equal guidance_key and parameters, and runs admitted requests concurrently on
+ * `slots` CUDA streams, each with its own workspace (continuous batching: a request is admitted as
+ * soon as a slot and memory are free). Results are bit-identical to hgf_aggregate on the same
+ * inputs, whatever else is in flight. Device memory for cached guidances is allocated stream-
+ * ordered (cudaMallocAsync) so that admission never synchronises the device.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct hgf_server hgf_server;
+
+typedef struct {
+  uint64_t guidance_key;  /* requests with equal keys, shapes and params share one guidance */
+  const float *img;       /* device, C x H x W float32; read only when the guidance is prepared */
+  int C, H, W;
+  hgf_params params;
+  const void *cost;       /* device, L x H x W of cost_dtype */
+  int cost_dtype;
+  int L;
+  int32_t *labels;        /* device int32 H x W (required) */
+  float *best;            /* device float32 H x W or NULL */
+} hgf_request;
+
+typedef struct {
+  uint64_t submitted, completed, failed, rejected_busy, rejected_nomem;
+  uint64_t cache_hits, cache_misses, evictions;
+  double p50_ms, p99_ms, mean_ms, max_ms;  /* submit -> results written, completed requests */
+  double mpixel_labels_per_s;              /* completed H*W*L / (last completion - first submit) */
+  size_t budget_bytes, resident_bytes, peak_bytes;
+  int slots, max_concurrent;               /* slots, most requests seen running at once */
+} hgf_serve_stats_t;
+
+/* Create a server on `device` with a device-memory budget (slot workspaces + cached guidances),
+ * `slots` concurrent streams (1..16) and a queue of at most `max_queue` waiting requests. Each
+ * slot's workspace is allocated here for images up to max_pixels pixels and n <= max_n. */
+hgf_status hgf_serve_create(int device, size_t budget_bytes, int slots, int max_queue,
+                            int max_pixels, int max_n, hgf_server **out);
+/* Queue a request (the structure is copied; the buffers it points to must stay valid until the
+ * request completes). HGF_EBUSY: queue full. HGF_ENOMEM: the request alone exceeds the budget.
+ * HGF_EINVAL / HGF_EUNSUPPORTED: invalid request. *id receives the request id. */
+hgf_status hgf_serve_submit(hgf_server *s, const hgf_request *req, uint64_t *id);
+/* HGF_OK: results written; HGF_EAGAIN: queued or running; HGF_ECUDA: the request failed;
+ * HGF_EINVAL: unknown id. */
+hgf_status hgf_serve_poll(hgf_server *s, uint64_t id);
+/* Waits at most timeout_ms (< 0: no limit) for the request: HGF_OK, HGF_ETIMEOUT or as poll. */
+hgf_status hgf_serve_wait(hgf_server *s, uint64_t id, int timeout_ms);
+/* Statistics since creation (or the last reset when reset != 0, after reading them). */
+hgf_status hgf_serve_stats(hgf_server *s, hgf_serve_stats_t *out, int reset);
+/* Test hook: make the next `count` guidance allocations fail as if the device were out of memory
+ * (the affected requests complete with HGF_ENOMEM). */
+hgf_status hgf_serve_inject_alloc_failures(hgf_server *s, int count);
+/* Drain the queue, wait for running requests, free everything. NULL is accepted. */
+hgf_status hgf_serve_destroy(hgf_server *s);
+
 /* Instrumentation (no counterpart in the paper). hgf_launch_count: number of kernels this context
  * has launched since creation. hgf_profile_enable: when on, every kernel launch is bracketed by a
  * CUDA event pair on its stream. hgf_profile_report: waits for the recorded events, writes

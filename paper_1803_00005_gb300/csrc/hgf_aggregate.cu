@@ -71,7 +71,10 @@ __global__ void __launch_bounds__(NT) k_coef(const CT *__restrict__ cost, int H,
   constexpr int NG = basis_n(B), C1 = NG + 1, NC = basis_channels_in(B), RAW = NC + K;
   constexpr int P = NG * (NG + 1) / 2;
   constexpr int REC = record_floats(NG), CP = coef_floats(NG);
-  constexpr bool EARLY = REC <= 68;  // the record fits in registers: load it ahead of the scans
+#ifndef HGF_EARLY_RECORD_FLOATS
+#define HGF_EARLY_RECORD_FLOATS 68
+#endif
+  constexpr bool EARLY = REC <= HGF_EARLY_RECORD_FLOATS;  // record held in registers over the scans
   extern __shared__ __align__(16) float smem[];
   float *sA = smem;
   float *ring = smem + K * C1 * kRowStride;  // [2r+1][RAW][NT], thread-private columns

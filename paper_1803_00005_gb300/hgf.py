@@ -30,7 +30,8 @@ EXPORTED = [
     "hgf_prepare", "hgf_guidance_release", "hgf_guidance_info", "hgf_guidance_export",
     "hgf_aggregate", "hgf_aggregate_plain", "hgf_wta", "hgf_filter_host", "hgf_set_tuning",
     "hgf_guidance_update", "hgf_launch_count", "hgf_profile_enable", "hgf_profile_report",
-    "hgf_aggregate_static",
+    "hgf_aggregate_static", "hgf_serve_create", "hgf_serve_submit", "hgf_serve_poll",
+    "hgf_serve_wait", "hgf_serve_stats", "hgf_serve_inject_alloc_failures", "hgf_serve_destroy",
 ]
 
 
@@ -50,6 +51,26 @@ class hgf_params(ctypes.Structure):
 class hgf_tuning(ctypes.Structure):
     _fields_ = [("labels_per_pass", ctypes.c_int), ("band_rows", ctypes.c_int),
                 ("chunk_labels", ctypes.c_int), ("apply_mode", ctypes.c_int)]
+
+
+class hgf_request(ctypes.Structure):
+    _fields_ = [("guidance_key", ctypes.c_uint64), ("img", ctypes.c_void_p), ("C", ctypes.c_int),
+                ("H", ctypes.c_int), ("W", ctypes.c_int), ("params", hgf_params),
+                ("cost", ctypes.c_void_p), ("cost_dtype", ctypes.c_int), ("L", ctypes.c_int),
+                ("labels", ctypes.c_void_p), ("best", ctypes.c_void_p)]
+
+
+class hgf_serve_stats_t(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "completed", "failed", "rejected_busy",
+                                               "rejected_nomem", "cache_hits", "cache_misses",
+                                               "evictions")] + \
+               [(n, ctypes.c_double) for n in ("p50_ms", "p99_ms", "mean_ms", "max_ms",
+                                               "mpixel_labels_per_s")] + \
+               [(n, ctypes.c_size_t) for n in ("budget_bytes", "resident_bytes", "peak_bytes")] + \
+               [("slots", ctypes.c_int), ("max_concurrent", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 _lib = None
@@ -80,6 +101,13 @@ def lib():
         "hgf_aggregate": (c_int, [vp, vp, vp, c_int, c_int, vp, c_int, vp, vp, vp]),
         "hgf_aggregate_plain": (c_int, [vp, vp, vp, c_int, c_int, vp, c_int, vp, vp, vp]),
         "hgf_aggregate_static": (c_int, [vp, vp, vp, c_int, c_int, vp, c_int, vp, vp, vp]),
+        "hgf_serve_create": (c_int, [c_int, ctypes.c_size_t, c_int, c_int, c_int, c_int, P(vp)]),
+        "hgf_serve_submit": (c_int, [vp, P(hgf_request), P(ctypes.c_uint64)]),
+        "hgf_serve_poll": (c_int, [vp, ctypes.c_uint64]),
+        "hgf_serve_wait": (c_int, [vp, ctypes.c_uint64, c_int]),
+        "hgf_serve_stats": (c_int, [vp, P(hgf_serve_stats_t), c_int]),
+        "hgf_serve_inject_alloc_failures": (c_int, [vp, c_int]),
+        "hgf_serve_destroy": (c_int, [vp]),
         "hgf_wta": (c_int, [vp, vp, c_int, c_int, c_int, c_int, vp, vp, vp]),
         "hgf_filter_host": (c_int, [vp, vp, c_int, c_int, c_int, P(hgf_params), vp, c_int, c_int,
                                     vp, vp, vp]),
@@ -275,3 +303,54 @@ def hgf_profile_report(ctx):
     buf = ctypes.create_string_buffer(1 << 16)
     _check(ctx, lib().hgf_profile_report(ctx, buf, len(buf)))
     return json.loads(buf.value.decode())
+
+
+# ------------------------------------------------------------------------------------ serving
+def hgf_serve_create(device=0, budget_bytes=8 << 30, slots=4, max_queue=256,
+                     max_pixels=1920 * 1080, max_n=19):
+    h = ctypes.c_void_p()
+    st = lib().hgf_serve_create(int(device), int(budget_bytes), int(slots), int(max_queue),
+                                int(max_pixels), int(max_n), ctypes.byref(h))
+    if st != HGF_OK:
+        raise HGFError(st, "hgf_serve_create failed")
+    return h
+
+
+def make_request(guidance_key, img, cost, params, labels, best=None):
+    """Request structure for device tensors img (C, H, W), cost (L, H, W), labels (H, W)."""
+    C, H, W = img.shape
+    return hgf_request(guidance_key=int(guidance_key), img=img.data_ptr(), C=C, H=H, W=W,
+                       params=params, cost=cost.data_ptr(), cost_dtype=_dtype_code(cost),
+                       L=cost.shape[0], labels=labels.data_ptr(),
+                       best=None if best is None else best.data_ptr())
+
+
+def hgf_serve_submit(server, req):
+    """Returns (status, id); status is HGF_OK, HGF_EBUSY, HGF_ENOMEM, ..."""
+    rid = ctypes.c_uint64()
+    st = lib().hgf_serve_submit(server, ctypes.byref(req), ctypes.byref(rid))
+    return st, rid.value
+
+
+def hgf_serve_poll(server, rid):
+    return lib().hgf_serve_poll(server, ctypes.c_uint64(rid))
+
+
+def hgf_serve_wait(server, rid, timeout_ms=-1):
+    return lib().hgf_serve_wait(server, ctypes.c_uint64(rid), int(timeout_ms))
+
+
+def hgf_serve_stats(server, reset=False):
+    s = hgf_serve_stats_t()
+    st = lib().hgf_serve_stats(server, ctypes.byref(s), 1 if reset else 0)
+    if st != HGF_OK:
+        raise HGFError(st, "hgf_serve_stats")
+    return s.as_dict()
+
+
+def hgf_serve_inject_alloc_failures(server, count):
+    return lib().hgf_serve_inject_alloc_failures(server, int(count))
+
+
+def hgf_serve_destroy(server):
+    lib().hgf_serve_destroy(server)

@@ -17,7 +17,8 @@ import dataclasses
 import numpy as np
 
 __all__ = [
-    "StereoCase", "stereo_pair", "cost_volume", "make_case", "to_dtype", "CONFIG_SMALL",
+    "StereoCase", "stereo_pair", "cost_volume", "cost_volume_torch", "make_case", "to_dtype",
+    "CONFIG_SMALL",
     "CONFIG_QUARTER", "CONFIG_LARGE", "batched_cases", "serving_requests",
 ]
 
@@ -144,6 +145,32 @@ def cost_volume(left: np.ndarray, right: np.ndarray, n_labels: int, dtype: str =
         if out is None:
             out = np.empty((len(labels), H, W), dtype=s.dtype)
         out[k] = s
+    return out
+
+
+def cost_volume_torch(left, right, n_labels: int, dtype: str = "bf16", device="cuda"):
+    """The same V(x, y, l) as cost_volume, built with torch on `device` (for large serving
+    inputs); float32 arithmetic, then rounded to the storage dtype. Returns a torch tensor."""
+    import torch
+    Lt = torch.as_tensor(left, dtype=torch.float32, device=device)
+    Rt = torch.as_tensor(right, dtype=torch.float32, device=device)
+    _, H, W = Lt.shape
+
+    def gx(img):
+        g = img.mean(dim=0)
+        xp = torch.clamp(torch.arange(W, device=device) + 1, max=W - 1)
+        xm = torch.clamp(torch.arange(W, device=device) - 1, min=0)
+        return 0.5 * (g[:, xp] - g[:, xm])
+
+    gl, gr = gx(Lt), gx(Rt)
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[dtype]
+    out = torch.empty((n_labels, H, W), dtype=tdt, device=device)
+    x = torch.arange(W, device=device)
+    for l in range(n_labels):
+        xs = torch.clamp(x - l, min=0)
+        col = (Lt - Rt[:, :, xs]).abs().mean(dim=0)
+        grd = (gl - gr[:, xs]).abs()
+        out[l] = (0.9 * torch.clamp(col, max=0.028) + 0.1 * torch.clamp(grd, max=0.008)).to(tdt)
     return out
 
 
