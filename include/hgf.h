@@ -169,6 +169,34 @@ typedef struct {
 hgf_status hgf_set_tuning(hgf_ctx *ctx, const hgf_tuning *t);
 
 /* ---------------------------------------------------------------------------------------------
+ * Batches (no counterpart in the paper): many images of different sizes, label counts and
+ * guidance degrees processed together. hgf_batch_create allocates, once, every job's guidance
+ * handle and the workspaces of `streams` internal CUDA streams (jobs are spread over them,
+ * largest first, to balance the work). hgf_batch_run enqueues every job (guidance precompute +
+ * fused aggregation + WTA) on those streams, forked from and joined back into `stream` by events:
+ * it allocates nothing, so it can be captured into a CUDA graph; hgf_batch_launch_graph captures
+ * it once into a graph (instantiated on the first call) and launches that graph. Job results are
+ * the same as hgf_prepare + hgf_aggregate on each job alone.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct hgf_batch hgf_batch;
+typedef struct {
+  const float *img;   /* device C x H x W float32 */
+  int C, H, W;
+  hgf_params params;
+  const void *cost;   /* device L x H x W of cost_dtype */
+  int cost_dtype;
+  int L;
+  int32_t *labels;    /* device int32 H x W or NULL */
+  float *best;        /* device float32 H x W or NULL */
+  float *filtered;    /* device float32 L x H x W or NULL (one output at least) */
+} hgf_job;
+hgf_status hgf_batch_create(hgf_ctx *ctx, const hgf_job *jobs, int njobs, int streams,
+                            hgf_batch **out);
+hgf_status hgf_batch_run(hgf_batch *b, void *stream);
+hgf_status hgf_batch_launch_graph(hgf_batch *b, void *stream);
+hgf_status hgf_batch_destroy(hgf_batch *b);
+
+/* ---------------------------------------------------------------------------------------------
  * Serving (no counterpart in the paper): a request loop in a background thread that admits
  * multi-label jobs of different sizes, label counts and guidance degrees against a device-memory
  * budget, keeps each guidance's resident inverse (hgf_prepare) in an LRU cache shared by

@@ -26,27 +26,43 @@ namespace {
 constexpr int NT = kStripThreads;
 constexpr int kRowStride = NT + 4;  // [0..3] padding (index 3 holds the zero prefix), 4+t values
 
-// Inclusive prefix sums along each shared row (values at [4 .. 4+NT)), one warp per row.
+// Inclusive prefix sums along each shared row (values at [4 .. 4+NT)), one warp per row; two
+// rows per iteration with both loads issued first so that their shuffle chains overlap.
+__device__ __forceinline__ void scan4(float4 &v, int lane) {
+  v.y += v.x;
+  v.z += v.y;
+  v.w += v.z;
+  float tot = v.w;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    float o = __shfl_up_sync(0xffffffffu, tot, off);
+    if (lane >= off) tot += o;
+  }
+  const float ex = tot - v.w;
+  v.x += ex;
+  v.y += ex;
+  v.z += ex;
+  v.w += ex;
+}
+
 __device__ __forceinline__ void scan_rows(float *sA, int rows) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int row = warp; row < rows; row += NT / 32) {
-    float4 *p = reinterpret_cast<float4 *>(sA + row * kRowStride + 4) + lane;
-    float4 v = *p;
-    v.y += v.x;
-    v.z += v.y;
-    v.w += v.z;
-    float tot = v.w;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      float o = __shfl_up_sync(0xffffffffu, tot, off);
-      if (lane >= off) tot += o;
-    }
-    float ex = tot - v.w;
-    v.x += ex;
-    v.y += ex;
-    v.z += ex;
-    v.w += ex;
-    *p = v;
+  constexpr int NW = NT / 32;
+  int row = warp;
+  for (; row + NW < rows; row += 2 * NW) {
+    float4 *p0 = reinterpret_cast<float4 *>(sA + row * kRowStride + 4) + lane;
+    float4 *p1 = reinterpret_cast<float4 *>(sA + (row + NW) * kRowStride + 4) + lane;
+    float4 v0 = *p0, v1 = *p1;
+    scan4(v0, lane);
+    scan4(v1, lane);
+    *p0 = v0;
+    *p1 = v1;
+  }
+  if (row < rows) {
+    float4 *p0 = reinterpret_cast<float4 *>(sA + row * kRowStride + 4) + lane;
+    float4 v0 = *p0;
+    scan4(v0, lane);
+    *p0 = v0;
   }
 }
 
@@ -57,7 +73,7 @@ __device__ __forceinline__ float window(const float *row, int t, int r) {
 
 template <int B, int K>
 constexpr size_t coef_smem_bytes(int r) {
-  return sizeof(float) * ((size_t)K * (basis_n(B) + 1) * kRowStride +
+  return sizeof(float) * ((size_t)2 * K * (basis_n(B) + 1) * kRowStride +
                           (size_t)(2 * r + 1) * (basis_channels_in(B) + K) * NT);
 }
 
@@ -76,8 +92,10 @@ __global__ void __launch_bounds__(NT) k_coef(const CT *__restrict__ cost, int H,
 #endif
   constexpr bool EARLY = REC <= HGF_EARLY_RECORD_FLOATS;  // record held in registers over the scans
   extern __shared__ __align__(16) float smem[];
-  float *sA = smem;
-  float *ring = smem + K * C1 * kRowStride;  // [2r+1][RAW][NT], thread-private columns
+  // two scan buffers used on alternate rows: a warp may start the next row's vertical update
+  // while others still read this row's window sums, so no barrier is needed at the end of a row
+  float *sA0 = smem;
+  float *ring = smem + 2 * K * C1 * kRowStride;  // [2r+1][RAW][NT], thread-private columns
   const int R = 2 * r + 1;
   const size_t HW = (size_t)H * W;
   const int t = threadIdx.x;
@@ -92,7 +110,7 @@ __global__ void __launch_bounds__(NT) k_coef(const CT *__restrict__ cost, int H,
   const int add_lo = max(0, Y0 - r);
   const int s_begin = Y0 - r, s_end = Y1 + r;
 
-  for (int i = t; i < K * C1; i += NT) sA[i * kRowStride + 3] = 0.f;
+  for (int i = t; i < 2 * K * C1; i += NT) sA0[i * kRowStride + 3] = 0.f;
   float sh[NG];
 #pragma unroll
   for (int i = 0; i < NG; ++i) sh[i] = __ldg(shift + i);
@@ -175,6 +193,7 @@ __global__ void __launch_bounds__(NT) k_coef(const CT *__restrict__ cost, int H,
       }
     }
     if (y1 < Y0) return;  // warm-up rows: no coefficient row complete yet (uniform per CTA)
+    float *sA = sA0 + ((y1 - Y0) & 1) * K * C1 * kRowStride;
 
     // ---- phase B: horizontal window sums via inclusive prefix scans
 #pragma unroll
@@ -237,7 +256,6 @@ __global__ void __launch_bounds__(NT) k_coef(const CT *__restrict__ cost, int H,
         }
       }
     }
-    __syncthreads();
   };
   for (int s = s_begin; s < s_end; s += 3) {
     step(s, pa, pc);
@@ -248,7 +266,7 @@ __global__ void __launch_bounds__(NT) k_coef(const CT *__restrict__ cost, int H,
 
 template <int B, bool RING>
 constexpr size_t apply_smem_bytes(int r) {
-  return sizeof(float) * ((size_t)(basis_n(B) + 1) * kRowStride +
+  return sizeof(float) * ((size_t)2 * (basis_n(B) + 1) * kRowStride +
                           (RING ? (size_t)(2 * r + 1) * (basis_n(B) + 1) * NT : 0));
 }
 
@@ -263,8 +281,8 @@ __global__ void __launch_bounds__(NT) k_apply(const float *__restrict__ coef, in
                                               int band_rows) {
   constexpr int NG = basis_n(B), C1 = NG + 1, NC = basis_channels_in(B), CP = coef_floats(NG);
   extern __shared__ __align__(16) float smem[];
-  float *sA = smem;
-  float *ring = smem + C1 * kRowStride;  // [2r+1][C1][NT]
+  float *sA0 = smem;                         // two scan buffers, alternate rows (see k_coef)
+  float *ring = smem + 2 * C1 * kRowStride;  // [2r+1][C1][NT]
   const int R = 2 * r + 1;
   const size_t HW = (size_t)H * W;
   const int t = threadIdx.x;
@@ -278,7 +296,7 @@ __global__ void __launch_bounds__(NT) k_apply(const float *__restrict__ coef, in
   const int add_lo = max(0, Y0 - r);
   const int s_begin = Y0 - r, s_end = Y1 + r;
 
-  if (t < C1) sA[t * kRowStride + 3] = 0.f;
+  if (t < 2 * C1) sA0[t * kRowStride + 3] = 0.f;
   float sh[NG];
 #pragma unroll
   for (int i = 0; i < NG; ++i) sh[i] = __ldg(shift + i);
@@ -354,6 +372,7 @@ __global__ void __launch_bounds__(NT) k_apply(const float *__restrict__ coef, in
       }
     }
     if (y2 < Y0) return;
+    float *sA = sA0 + ((y2 - Y0) & 1) * C1 * kRowStride;
 
 #pragma unroll
     for (int c = 0; c < C1; ++c) sA[c * kRowStride + 4 + t] = V[c];
@@ -374,7 +393,6 @@ __global__ void __launch_bounds__(NT) k_apply(const float *__restrict__ coef, in
       if (filtered) filtered[(size_t)label * HW + pix] = q;
       if (keys) atomicMin(keys + pix, wta_key(q, label));
     }
-    __syncthreads();
   };
   for (int s = s_begin; s < s_end; s += 3) {
     step(s, pa, pc, oa, oc);
@@ -419,7 +437,10 @@ cudaError_t set_smem(Kern k, size_t bytes) {
 }
 
 // Rows per band for a kernel whose grid is strips x bands x slabs: the band count that minimises
-// (waves of resident CTAs) x (rows streamed per CTA, including the 2r warm-up rows).
+// (waves of resident CTAs) x (rows streamed per CTA, including the 2r warm-up rows). Callers pass
+// a nominal slab count that depends on the shape only (not on how many labels a call or chunk
+// has): the band boundaries decide the order of the running sums, so results are then identical
+// whether an image is aggregated alone, in a batch, in the serving loop or in label chunks.
 static int choose_band_rows(int H, int r, long long strips_slabs, int resident) {
   long long best_cost = -1;
   int best = H;
@@ -435,6 +456,8 @@ static int choose_band_rows(int H, int r, long long strips_slabs, int resident) 
   }
   return best;
 }
+
+constexpr int kNominalLabels = 64;  // label count the band heights are planned for
 
 template <typename Kern>
 static int resident_ctas(Kern k, size_t smem) {
@@ -458,15 +481,23 @@ cudaError_t launch_chunk(const hgf_guidance *g, const void *cost, int cost_dtype
   cudaError_t e;
   {
     const size_t sm = coef_smem_bytes<B, K>(r);
+    // the shared-memory limit is raised before the occupancy query so that every call (the
+    // first included) plans the same bands
+    e = set_smem(k_coef<B, K, float>, sm);
+    if (e == cudaSuccess) e = set_smem(k_coef<B, K, __nv_bfloat16>, sm);
+    if (e == cudaSuccess) e = set_smem(k_coef<B, K, __half>, sm);
+    if (e != cudaSuccess) return e;
     const int passes = (nc + K - 1) / K;
+    // bands planned for the two-label kernel whatever K is, so that K never changes a result
+    const size_t sm2 = coef_smem_bytes<B, 2>(r);
+    e = set_smem(k_coef<B, 2, float>, sm2);
+    if (e != cudaSuccess) return e;
     const int rows = band_rows > 0 ? band_rows
-                                   : choose_band_rows(H, r, (long long)strips * passes,
-                                                      resident_ctas(k_coef<B, K, float>, sm));
+                                   : choose_band_rows(H, r, (long long)strips * (kNominalLabels / 2),
+                                                      resident_ctas(k_coef<B, 2, float>, sm2));
     dim3 grid(strips, (H + rows - 1) / rows, passes);
     LaunchScope ls(prof, "k_coef", s);
 #define HGF_COEF(CT)                                                                          \
-  e = set_smem(k_coef<B, K, CT>, sm);                                                         \
-  if (e != cudaSuccess) return e;                                                             \
   k_coef<B, K, CT><<<grid, NT, sm, s>>>((const CT *)cost, H, W, r, g->img, g->shift, g->rec,  \
                                         coef_ws, l_first, nc, rows);
     switch (cost_dtype) {
@@ -481,22 +512,22 @@ cudaError_t launch_chunk(const hgf_guidance *g, const void *cost, int cost_dtype
     LaunchScope ls(prof, "k_apply", s);
     const size_t ring_sm = apply_smem_bytes<B, true>(r);
     if (apply_ring && ring_sm <= 227 * 1024) {
-      const int rows = band_rows > 0 ? band_rows
-                                     : choose_band_rows(H, r, (long long)strips * nc,
-                                                        resident_ctas(k_apply<B, true>, ring_sm));
-      dim3 grid(strips, (H + rows - 1) / rows, nc);
       e = set_smem(k_apply<B, true>, ring_sm);
       if (e != cudaSuccess) return e;
+      const int rows = band_rows > 0 ? band_rows
+                                     : choose_band_rows(H, r, (long long)strips * kNominalLabels,
+                                                        resident_ctas(k_apply<B, true>, ring_sm));
+      dim3 grid(strips, (H + rows - 1) / rows, nc);
       k_apply<B, true><<<grid, NT, ring_sm, s>>>(coef_ws, H, W, r, g->img, g->shift, keys,
                                                  filtered, l_first, rows);
     } else {
       const size_t sm = apply_smem_bytes<B, false>(r);
-      const int rows = band_rows > 0 ? band_rows
-                                     : choose_band_rows(H, r, (long long)strips * nc,
-                                                        resident_ctas(k_apply<B, false>, sm));
-      dim3 grid(strips, (H + rows - 1) / rows, nc);
       e = set_smem(k_apply<B, false>, sm);
       if (e != cudaSuccess) return e;
+      const int rows = band_rows > 0 ? band_rows
+                                     : choose_band_rows(H, r, (long long)strips * kNominalLabels,
+                                                        resident_ctas(k_apply<B, false>, sm));
+      dim3 grid(strips, (H + rows - 1) / rows, nc);
       k_apply<B, false><<<grid, NT, sm, s>>>(coef_ws, H, W, r, g->img, g->shift, keys, filtered,
                                              l_first, rows);
     }
@@ -517,7 +548,8 @@ bool aggregate_supported(int n) {
 
 // Dynamic shared memory of k_coef for n guidance channels, C input channels, K labels, radius r.
 static size_t coef_smem(int n, int C, int K, int r) {
-  return sizeof(float) * ((size_t)K * (n + 1) * kRowStride + (size_t)(2 * r + 1) * (C + K) * NT);
+  return sizeof(float) *
+         ((size_t)2 * K * (n + 1) * kRowStride + (size_t)(2 * r + 1) * (C + K) * NT);
 }
 
 bool aggregate_fits(const hgf_guidance *g) {
@@ -526,10 +558,13 @@ bool aggregate_fits(const hgf_guidance *g) {
 
 AggregatePlan plan_aggregate(const hgf_guidance *g, int L, const hgf_tuning &t, int num_sms) {
   AggregatePlan p;
-  // two labels per pass (measured faster than four: the four-label kernel runs out of registers)
-  p.K = 2;
-  if (t.labels_per_pass == 2 || (t.labels_per_pass == 4 &&
-                                 coef_smem(g->n, g->C, 4, g->r) <= 227 * 1024))
+  // four labels per pass on large images (1400x1100, n = 9: 18.3 vs 22.5 ms), two on small ones
+  // (450x375, n = 9: 0.51 vs 0.54 ms); four only while two CTAs still fit on an SM. The choice
+  // does not change results (each label's arithmetic is the same for any K).
+  const bool large = (long long)g->H * g->W >= 500000;
+  p.K = (large && g->n < 19 && coef_smem(g->n, g->C, 4, g->r) <= 113 * 1024) ? 4 : 2;
+  if (t.labels_per_pass == 1 || t.labels_per_pass == 2 ||
+      (t.labels_per_pass == 4 && coef_smem(g->n, g->C, 4, g->r) <= 227 * 1024))
     p.K = t.labels_per_pass;
   const size_t plane = (size_t)coef_floats(g->n) * g->H * g->W * sizeof(float);
   // labels per chunk: all labels while the coefficient workspace stays under 4 GiB
@@ -541,7 +576,7 @@ AggregatePlan plan_aggregate(const hgf_guidance *g, int L, const hgf_tuning &t, 
   const int passes = (p.chunk + p.K - 1) / p.K;
   // the outgoing coefficient rows of the output kernel are reloaded by default: they were read
   // 2r+1 steps earlier and are still in L2, and without the ring more CTAs fit on an SM
-  const size_t ring = sizeof(float) * (size_t)(g->n + 1) * ((2 * g->r + 1) * NT + kRowStride);
+  const size_t ring = sizeof(float) * (size_t)(g->n + 1) * ((2 * g->r + 1) * NT + 2 * kRowStride);
   p.apply_ring = t.apply_mode == 1 && ring <= 227 * 1024;
   (void)strips;
   (void)passes;
@@ -574,6 +609,9 @@ cudaError_t launch_aggregate(const hgf_guidance *g, const void *cost, int cost_d
       const int nc = std::min(p.chunk, L - l0);
       if (p.K == 4)
         e = launch_chunk<B, 4>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, k, p.band_rows,
+                               p.apply_ring, s, prof);
+      else if (p.K == 1)
+        e = launch_chunk<B, 1>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, k, p.band_rows,
                                p.apply_ring, s, prof);
       else
         e = launch_chunk<B, 2>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, k, p.band_rows,

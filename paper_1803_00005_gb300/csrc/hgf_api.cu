@@ -212,6 +212,21 @@ hgf_status aggregate_locked(hgf_ctx *ctx, const hgf_guidance *g, const void *cos
 
 }  // namespace
 
+namespace hgf {
+hgf_status alloc_guidance_checked(hgf_ctx *ctx, int C, int H, int W, const hgf_params *p,
+                                  hgf_guidance **out) {
+  int n = 0;
+  hgf_status st = check_params(ctx, C, H, W, p, &n);
+  if (st != HGF_OK) return st;
+  return alloc_guidance(ctx, C, H, W, n, p, out);
+}
+void free_guidance(hgf_guidance *g) {
+  if (!g) return;
+  cudaFree(g->rec);
+  delete g;
+}
+}  // namespace hgf
+
 extern "C" {
 
 int hgf_num_channels(int C, int degree, int basis) {

@@ -193,6 +193,10 @@ cudaError_t launch_aggregate_plain(const hgf_guidance *g, const void *cost, int 
 cudaError_t launch_wta(const float *filtered, int L, int H, int W, int32_t *labels, float *best,
                        cudaStream_t s, Profiler *prof);
 bool aggregate_supported(int n);
+// Guidance handle allocation (cudaMalloc) after argument checks; free_guidance releases it.
+hgf_status alloc_guidance_checked(hgf_ctx *ctx, int C, int H, int W, const hgf_params *p,
+                                  hgf_guidance **out);
+void free_guidance(hgf_guidance *g);
 bool aggregate_fits(const hgf_guidance *g);  // fused kernels take this shape
 
 }  // namespace hgf

@@ -32,6 +32,7 @@ EXPORTED = [
     "hgf_guidance_update", "hgf_launch_count", "hgf_profile_enable", "hgf_profile_report",
     "hgf_aggregate_static", "hgf_serve_create", "hgf_serve_submit", "hgf_serve_poll",
     "hgf_serve_wait", "hgf_serve_stats", "hgf_serve_inject_alloc_failures", "hgf_serve_destroy",
+    "hgf_batch_create", "hgf_batch_run", "hgf_batch_launch_graph", "hgf_batch_destroy",
 ]
 
 
@@ -58,6 +59,13 @@ class hgf_request(ctypes.Structure):
                 ("H", ctypes.c_int), ("W", ctypes.c_int), ("params", hgf_params),
                 ("cost", ctypes.c_void_p), ("cost_dtype", ctypes.c_int), ("L", ctypes.c_int),
                 ("labels", ctypes.c_void_p), ("best", ctypes.c_void_p)]
+
+
+class hgf_job(ctypes.Structure):
+    _fields_ = [("img", ctypes.c_void_p), ("C", ctypes.c_int), ("H", ctypes.c_int),
+                ("W", ctypes.c_int), ("params", hgf_params), ("cost", ctypes.c_void_p),
+                ("cost_dtype", ctypes.c_int), ("L", ctypes.c_int), ("labels", ctypes.c_void_p),
+                ("best", ctypes.c_void_p), ("filtered", ctypes.c_void_p)]
 
 
 class hgf_serve_stats_t(ctypes.Structure):
@@ -108,6 +116,10 @@ def lib():
         "hgf_serve_stats": (c_int, [vp, P(hgf_serve_stats_t), c_int]),
         "hgf_serve_inject_alloc_failures": (c_int, [vp, c_int]),
         "hgf_serve_destroy": (c_int, [vp]),
+        "hgf_batch_create": (c_int, [vp, P(hgf_job), c_int, c_int, P(vp)]),
+        "hgf_batch_run": (c_int, [vp, vp]),
+        "hgf_batch_launch_graph": (c_int, [vp, vp]),
+        "hgf_batch_destroy": (c_int, [vp]),
         "hgf_wta": (c_int, [vp, vp, c_int, c_int, c_int, c_int, vp, vp, vp]),
         "hgf_filter_host": (c_int, [vp, vp, c_int, c_int, c_int, P(hgf_params), vp, c_int, c_int,
                                     vp, vp, vp]),
@@ -354,3 +366,32 @@ def hgf_serve_inject_alloc_failures(server, count):
 
 def hgf_serve_destroy(server):
     lib().hgf_serve_destroy(server)
+
+
+# -------------------------------------------------------------------------------------- batches
+def make_job(img, cost, params, labels=None, best=None, filtered=None):
+    C, H, W = img.shape
+    return hgf_job(img=img.data_ptr(), C=C, H=H, W=W, params=params, cost=cost.data_ptr(),
+                   cost_dtype=_dtype_code(cost), L=cost.shape[0],
+                   labels=None if labels is None else labels.data_ptr(),
+                   best=None if best is None else best.data_ptr(),
+                   filtered=None if filtered is None else filtered.data_ptr())
+
+
+def hgf_batch_create(ctx, jobs, streams=8):
+    arr = (hgf_job * len(jobs))(*jobs)
+    h = ctypes.c_void_p()
+    _check(ctx, lib().hgf_batch_create(ctx, arr, len(jobs), int(streams), ctypes.byref(h)))
+    return h
+
+
+def hgf_batch_run(ctx, batch, stream=None):
+    _check(ctx, lib().hgf_batch_run(batch, _stream(stream)))
+
+
+def hgf_batch_launch_graph(ctx, batch, stream=None):
+    _check(ctx, lib().hgf_batch_launch_graph(batch, _stream(stream)))
+
+
+def hgf_batch_destroy(batch):
+    lib().hgf_batch_destroy(batch)

@@ -226,3 +226,19 @@ def test_invalid_arguments_rejected(ctx):
     with pytest.raises(hgf.HGFError):
         hgf.hgf_aggregate(ctx, g, torch.rand((2, 8, 8), device="cuda"))  # no output requested
     hgf.hgf_guidance_release(g)
+
+
+def test_results_independent_of_label_chunking(ctx):
+    """Label chunking (workspace size) and labels per pass do not change any result bit: the band
+    boundaries of the running sums depend on the image shape only. (Explicit band_rows or
+    apply_mode tuning does change the rounding, within the tolerance.)"""
+    from paper_1803_00005_gb300 import hgf
+    case = synth.make_case(330, 210, 23, 111)
+    base = run_path(ctx, case.guidance, case.cost, "f32", 2, 9, 1e-4)
+    try:
+        for chunk, K in ((5, 2), (1, 2), (8, 4), (23, 4)):
+            hgf.hgf_set_tuning(ctx, labels_per_pass=K, chunk_labels=chunk)
+            got = run_path(ctx, case.guidance, case.cost, "f32", 2, 9, 1e-4)
+            assert np.array_equal(got[0], base[0]) and np.array_equal(got[1], base[1])
+    finally:
+        hgf.hgf_set_tuning(ctx)
