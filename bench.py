@@ -53,6 +53,40 @@ def flops_per_unit(kernel: str, n: int) -> tuple[float, str] | None:
     return None
 
 
+def profiled_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of `kernel` on
+    `workload` from profiles/ncu_traffic.md, or None when there is no capture or the kernel's
+    source file has changed since (the capture records a sha256 prefix of that file)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.md")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        cells = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(cells) == 5 and cells[0] == kernel and cells[1] == workload:
+            src = os.path.join(ROOT, cells[3])
+            if not os.path.exists(src):
+                return None
+            sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+            return float(cells[2]) if sha == cells[4] else None
+    return None
+
+
+def world_max(x: float, dist, device) -> float:
+    """Maximum of a per-rank float over all ranks (device: where the collective's tensor lives:
+    CUDA for NCCL, CPU for gloo)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_rank: float, world: int, t_max_s: float) -> float:
+    """Whole-job throughput in Mpixel*labels/s: every replica processes the same units; the job
+    takes as long as the slowest rank."""
+    return world * units_per_rank / t_max_s / 1e6
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -385,13 +419,9 @@ def main():
     clk = clocks.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     t_dev = sum(step_ms) / 1e3
-    t_max = t_dev
-    if world > 1:
-        tt = torch.tensor([t_dev], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = world_max(t_dev, dist, dev) if world > 1 else t_dev
     units = H * W * L * args.steps
-    value = world * units / t_max / 1e6
+    value = whole_job_value(units, world, t_max)
 
     # roofline of the dominant kernel (largest share of the profiled time)
     kernels = {k: dict(launches=v["launches"], ms_per_step=v["ms"] / args.steps)
@@ -408,7 +438,7 @@ def main():
             achieved = per_unit * units_per_launch / avg_s / 1e12
             peak = FP64_PEAK_TFLOPS if dom == "k_inverse" else FP32_PEAK_TFLOPS
             roof = dict(bound="alu", kernel=dom, achieved=achieved, peak=peak, unit="TFLOP/s",
-                        frac=achieved / peak, traffic=None,
+                        frac=achieved / peak, traffic=profiled_traffic(dom, args.workload),
                         model=f"{per_unit:.0f} flops per {uname}",
                         peak_note=("nominal float64 rate" if dom == "k_inverse" else
                                    "152 SMs x 128 FP32 lanes x 2 x 2070 MHz"))
@@ -429,10 +459,8 @@ def main():
         te = time.perf_counter() - t0
         hgf.hgf_destroy(hctx)
         if world > 1:
-            tt = torch.tensor([te], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
-        e2e = dict(value=world * units / te / 1e6, unit=UNIT,
+            te = world_max(te, dist, dev)
+        e2e = dict(value=whole_job_value(units, world, te), unit=UNIT,
                    h2d_bytes_per_step=int(pin_img.numel() * 4 + pin_cost.numel() *
                                           pin_cost.element_size()),
                    d2h_bytes_per_step=int(H * W * 4))
