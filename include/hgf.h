@@ -56,13 +56,24 @@ typedef enum { HGF_BASIS_MONOMIAL = 0, HGF_BASIS_POWERS = 1 } hgf_basis;
  * multiply-adds of S alpha and the cancellation of lambda^-1 against it. */
 typedef enum { HGF_COMBINE_ALPHA = 0, HGF_COMBINE_W3 = 1 } hgf_combine;
 
+/* Which filter (the two are different filters, not rounding variants of one another).
+ * CENTRED (default, Sec. 5.1): mu = A(G), Sigma = A(G G^T) - mu mu^T, a = (Sigma + eps E)^-1 cov,
+ *   b = A(p) - a^T mu, q = sum_i A(a_i) G_i + A(b); eps is in units of window means.
+ * PAPER (Sec. 3 and 4, Eqs. HGF_Iij, HGF_w3, HGF_z2): G_0 = 1 joins the guidance, the
+ *   (n+1) x (n+1) Gram matrix of window sums B(G_i G_j) (i, j = 0..n) and b_k = B(G_k p) are
+ *   uncentred, w = (lambda E + Gram)^-1 b penalises all n+1 weights with lambda = eps in units of
+ *   window sums, and Z = sum_{i>=1} A(w_i) G_i + A(w_0). Served by the fused path only
+ *   (hgf_aggregate_plain, hgf_guidance_export and windows with 2r+1 >= 128 give HGF_EUNSUPPORTED). */
+typedef enum { HGF_FORM_CENTRED = 0, HGF_FORM_PAPER = 1 } hgf_form;
+
 typedef struct {
   int degree;         /* polynomial degree d >= 1 (Sec. 4.2); n <= 19 */
   int basis;          /* hgf_basis */
   int r;              /* window radius r >= 0: (2r+1)^2 box (Sec. 6 uses r = 7) */
-  double eps;         /* regulariser eps > 0 added to the covariance of means (Sec. 5.1, lambda) */
+  double eps;         /* regulariser eps > 0 (lambda); units depend on `form` */
   int inv_precision;  /* HGF_F64 (default) or HGF_F32: precision of Sigma assembly + recursion */
   int combine;        /* hgf_combine */
+  int form;           /* hgf_form (0 = CENTRED) */
 } hgf_params;
 
 typedef struct hgf_ctx hgf_ctx;
@@ -156,7 +167,7 @@ hgf_status hgf_filter_host(hgf_ctx *ctx, const float *img, int C, int H, int W,
                            const hgf_params *params, const void *cost, int cost_dtype, int L,
                            int32_t *labels, float *best, void *stream);
 
-/* Tuning of the fused kernels (0 = automatic): labels per pass of the coefficient kernel (2 or 4),
+/* Tuning of the fused kernels (0 = automatic): labels per pass of the coefficient kernel (2, 4, 8),
  * row-band height, labels per chunk of the coefficient workspace, and how the output kernel gets
  * the row leaving its vertical window (1 = shared-memory ring, 2 = reload from device memory).
  * Returns HGF_EINVAL for values the kernels cannot take. */
@@ -251,11 +262,34 @@ hgf_status hgf_serve_inject_alloc_failures(hgf_server *s, int count);
 /* Drain the queue, wait for running requests, free everything. NULL is accepted. */
 hgf_status hgf_serve_destroy(hgf_server *s);
 
+/* ---------------------------------------------------------------------------------------------
+ * Batched inverse of regularised Gram matrices: the paper's comparison of its recursion against a
+ * per-matrix factorisation for many small matrices (Sec. 3, Fig. 1b). out_i = (lambda E + S_i)^-1
+ * for `count` symmetric n x n matrices S_i (n in 1..9 or 19), one GPU thread per matrix.
+ *   S, out: device float64, packed upper triangles row by row (n(n+1)/2 entries: (0,0), (0,1), ..,
+ *           (0,n-1), (1,1), ..), element-major over the batch: entry e of matrix i at
+ *           [e * count + i]. The caller owns both; they must not overlap.
+ *   method: HGF_INV_PROP1 (Prop. 1 recursion with lambda, inverse = -lambda alpha) or
+ *           HGF_INV_CHOLESKY (Cholesky factor of lambda E + S, inverse from the factor).
+ *   precision: HGF_F64 or HGF_F32 arithmetic (input and output stay float64).
+ * Enqueued on `stream`. HGF_EINVAL: NULL pointers, count < 1, lambda <= 0, unknown method or
+ * precision; HGF_EUNSUPPORTED: n not built. S_i must be positive semidefinite (Gram matrices);
+ * otherwise the result is unspecified (no error is detected). */
+typedef enum { HGF_INV_PROP1 = 0, HGF_INV_CHOLESKY = 1 } hgf_inverse_method;
+hgf_status hgf_batched_inverse(hgf_ctx *ctx, const double *S, int count, int n, double lambda,
+                               int method, int precision, double *out, void *stream);
+
 /* Instrumentation (no counterpart in the paper). hgf_launch_count: number of kernels this context
  * has launched since creation. hgf_profile_enable: when on, every kernel launch is bracketed by a
  * CUDA event pair on its stream. hgf_profile_report: waits for the recorded events, writes
  * {"kernel": {"launches": n, "ms": total}, ...} as JSON into buf (cap bytes) and clears them. */
 hgf_status hgf_launch_count(hgf_ctx *ctx, unsigned long long *out);
+/* Kernel watchdog (no counterpart in the paper). Every wait inside a kernel (for a bulk copy into
+ * shared memory) is bounded; a wait that runs out sets a per-device status word, the kernel stops
+ * its CTA early and that call's results are incomplete. hgf_device_status waits for all work on
+ * ctx's device, writes the word to *status (0: no wait ran out) and, when clear is nonzero,
+ * resets it. hgf_filter_host checks it itself and returns HGF_ETIMEOUT when it is set. */
+hgf_status hgf_device_status(hgf_ctx *ctx, int *status, int clear);
 hgf_status hgf_profile_enable(hgf_ctx *ctx, int enable);
 hgf_status hgf_profile_report(hgf_ctx *ctx, char *buf, size_t cap);
 

@@ -102,6 +102,8 @@ hgf_status check_params(hgf_ctx *ctx, int C, int H, int W, const hgf_params *p, 
     return set_err(ctx, HGF_EINVAL, "inv_precision must be HGF_F64 or HGF_F32");
   if (p->combine != HGF_COMBINE_ALPHA && p->combine != HGF_COMBINE_W3)
     return set_err(ctx, HGF_EINVAL, "unknown combine %d", p->combine);
+  if (p->form != HGF_FORM_CENTRED && p->form != HGF_FORM_PAPER)
+    return set_err(ctx, HGF_EINVAL, "unknown form %d", p->form);
   int n = hgf_num_channels(C, p->degree, p->basis);
   if (n < 1) return set_err(ctx, HGF_EUNSUPPORTED, "C=%d degree=%d basis=%d gives n > %d", C,
                             p->degree, p->basis, kMaxChannels);
@@ -129,8 +131,10 @@ hgf_status alloc_guidance(hgf_ctx *ctx, int C, int H, int W, int n, const hgf_pa
   g->eps = p->eps;
   g->inv_precision = p->inv_precision;
   g->combine = p->combine;
+  g->form = p->form;
   const size_t HW = (size_t)H * W;
-  const size_t floats = HW * ((size_t)C + n + packed_size(n) + n + record_floats(n)) + 64;
+  const size_t rec_floats = record_total_floats(H, W, n, g->r);
+  const size_t floats = HW * ((size_t)C + n + packed_size(n) + n) + rec_floats + 64;
   float *base = nullptr;
   cudaError_t e = cudaMalloc(&base, floats * sizeof(float));
   if (e != cudaSuccess) {
@@ -139,8 +143,8 @@ hgf_status alloc_guidance(hgf_ctx *ctx, int C, int H, int W, int n, const hgf_pa
     return set_err(ctx, HGF_ENOMEM, "cannot allocate %zu bytes for the guidance",
                    floats * sizeof(float));
   }
-  g->rec = base;  // first: float4 records need the allocation's alignment
-  g->img = g->rec + (size_t)record_floats(n) * HW;
+  g->rec = base;  // first: bulk copies of record blocks need the allocation's alignment
+  g->img = g->rec + rec_floats;
   g->G = g->img + (size_t)C * HW;
   g->minv = g->G + (size_t)n * HW;
   g->mu = g->minv + (size_t)packed_size(n) * HW;
@@ -152,7 +156,7 @@ hgf_status alloc_guidance(hgf_ctx *ctx, int C, int H, int W, int n, const hgf_pa
 bool same_shape(const hgf_guidance *g, int C, int H, int W, const hgf_params *p) {
   return g && g->C == C && g->H == H && g->W == W && g->degree == p->degree &&
          g->basis == p->basis && g->r == effective_radius(p->r, H, W) && g->eps == p->eps &&
-         g->inv_precision == p->inv_precision && g->combine == p->combine;
+         g->inv_precision == p->inv_precision && g->combine == p->combine && g->form == p->form;
 }
 
 hgf_status prepare_locked(hgf_ctx *ctx, hgf_guidance *g, const float *img, cudaStream_t s) {
@@ -185,6 +189,8 @@ hgf_status aggregate_locked(hgf_ctx *ctx, const hgf_guidance *g, const void *cos
                             int cost_dtype, int L, void *filtered, int32_t *labels, float *best,
                             cudaStream_t s) {
   if (!aggregate_fits(g)) {
+    if (g->form != HGF_FORM_CENTRED)
+      return set_err(ctx, HGF_EUNSUPPORTED, "the paper form needs 2r+1 < %d", kStripThreads);
     // windows too wide for the streaming kernels' shared-memory rings: the plain kernels
     // compute the same result for any radius
     int chunk = 1;
@@ -346,6 +352,8 @@ hgf_status hgf_guidance_export(hgf_ctx *ctx, const hgf_guidance *g, float *minv_
   hgf_status st = enter(ctx);
   if (st != HGF_OK) return st;
   if (!g || g->ctx != ctx) return set_err(ctx, HGF_EINVAL, "bad guidance handle");
+  if (g->form != HGF_FORM_CENTRED)
+    return set_err(ctx, HGF_EUNSUPPORTED, "export holds the centred form's inverse only");
   cudaError_t e = launch_export(g, minv_out, mu_out, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "hgf_guidance_export");
   return HGF_OK;
@@ -353,9 +361,9 @@ hgf_status hgf_guidance_export(hgf_ctx *ctx, const hgf_guidance *g, float *minv_
 
 hgf_status hgf_set_tuning(hgf_ctx *ctx, const hgf_tuning *t) {
   if (!ctx || !t) return HGF_EINVAL;
-  if (t->labels_per_pass != 0 && t->labels_per_pass != 1 && t->labels_per_pass != 2 &&
-      t->labels_per_pass != 4)
-    return set_err(ctx, HGF_EINVAL, "labels_per_pass must be 0, 1, 2 or 4");
+  if (t->labels_per_pass != 0 && t->labels_per_pass != 2 && t->labels_per_pass != 4 &&
+      t->labels_per_pass != 8)
+    return set_err(ctx, HGF_EINVAL, "labels_per_pass must be 0, 2, 4 or 8");
   if (t->band_rows < 0 || t->chunk_labels < 0)
     return set_err(ctx, HGF_EINVAL, "band_rows and chunk_labels must be >= 0");
   if (t->apply_mode < 0 || t->apply_mode > 2)
@@ -384,6 +392,8 @@ hgf_status hgf_aggregate_plain(hgf_ctx *ctx, const hgf_guidance *g, const void *
   if (st != HGF_OK) return st;
   st = check_outputs(ctx, g, cost, cost_dtype, L, filtered, filtered_dtype, labels, best);
   if (st != HGF_OK) return st;
+  if (g->form != HGF_FORM_CENTRED)
+    return set_err(ctx, HGF_EUNSUPPORTED, "the plain kernels compute the centred form only");
   cudaStream_t s = (cudaStream_t)stream;
   int chunk = 1;
   size_t need = plain_workspace_bytes(g, L, &chunk);
@@ -462,6 +472,40 @@ hgf_status hgf_filter_host(hgf_ctx *ctx, const float *img, int C, int H, int W,
   if (e == cudaSuccess && best) e = cudaMemcpyAsync(best, best_d, HW * 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail_locked(ctx, e, "hgf_filter_host download");
+  int status = 0;
+  e = read_device_status(&status, true);
+  if (e != cudaSuccess) return cuda_fail_locked(ctx, e, "hgf_filter_host status");
+  if (status != 0) return set_err(ctx, HGF_ETIMEOUT, "a bounded wait in a kernel ran out");
+  return HGF_OK;
+}
+
+hgf_status hgf_batched_inverse(hgf_ctx *ctx, const double *S, int count, int n, double lambda,
+                               int method, int precision, double *out, void *stream) {
+  hgf_status st = enter(ctx);
+  if (st != HGF_OK) return st;
+  if (!S || !out) return set_err(ctx, HGF_EINVAL, "NULL argument");
+  if (count < 1) return set_err(ctx, HGF_EINVAL, "count must be >= 1");
+  if (!(lambda > 0.0)) return set_err(ctx, HGF_EINVAL, "lambda must be > 0");
+  if (method != HGF_INV_PROP1 && method != HGF_INV_CHOLESKY)
+    return set_err(ctx, HGF_EINVAL, "unknown method %d", method);
+  if (precision != HGF_F64 && precision != HGF_F32)
+    return set_err(ctx, HGF_EINVAL, "precision must be HGF_F64 or HGF_F32");
+  if (!aggregate_supported(n)) return set_err(ctx, HGF_EUNSUPPORTED, "n = %d is not built", n);
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  cudaError_t e = launch_batched_inverse(S, count, n, lambda, method, precision, out,
+                                         (cudaStream_t)stream, &ctx->prof);
+  if (e != cudaSuccess) return cuda_fail_locked(ctx, e, "hgf_batched_inverse");
+  return HGF_OK;
+}
+
+hgf_status hgf_device_status(hgf_ctx *ctx, int *status, int clear) {
+  hgf_status st = enter(ctx);
+  if (st != HGF_OK) return st;
+  if (!status) return set_err(ctx, HGF_EINVAL, "NULL argument");
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = read_device_status(status, clear != 0);
+  if (e != cudaSuccess) return cuda_fail_locked(ctx, e, "hgf_device_status");
   return HGF_OK;
 }
 

@@ -1,0 +1,676 @@
+// Fused multi-label aggregation kernels (included by the hgf_fused_*.cu translation units, each
+// of which instantiates launch_basis for some guidance bases; the host side is hgf_aggregate.cu).
+//
+// Multi-label aggregation + WTA (Sec. 1 pipeline with the centred form of Sec. 5.1 and the
+// multipoint aggregation of Sec. 4.1, Eq. HGF_z1).
+//
+// Two streaming kernels per chunk of labels, both over vertical strips of the image (128 columns
+// per CTA, one thread per column, 2r of them halo) that walk down a band of rows:
+//   k_coef : vertical running sums of (p, G_1 p, .., G_n p) for K labels, horizontal window sums
+//            by prefix scans in shared memory, then per coefficient pixel
+//            cov = A(G p) - mu A(p), a = Minv cov, b = A(p) - a.mu, written to the workspace.
+//            The guidance G is recomputed from the input image (constant-index monomials).
+//   k_apply: vertical running sums of (b, a_1..a_n), horizontal window sums,
+//            q = sum_i A(a_i) G_i + A(b), and one packed 64-bit atomicMin per pixel (cost in the
+//            high word, label in the low word: lowest cost, then lowest label).
+// Every input row is read from device memory once: each thread keeps its column's last 2r+1 rows
+// in a private shared-memory ring (the row leaving the vertical window is subtracted from there)
+// and loads rows two steps ahead into registers, so the load latency overlaps two steps of work.
+// Windows are clipped at the image border: samples outside the image never enter a sum and the
+// means divide by the in-image count N(x, y).
+#pragma once
+#include "hgf_basis.cuh"
+
+#include <algorithm>
+
+namespace hgf {
+
+namespace {
+
+constexpr int NT = kStripThreads;
+constexpr int kRowStride = NT + 4;  // [0..3] padding (index 3 holds the zero prefix), 4+t values
+
+// Inclusive prefix sums along each shared row (values at [4 .. 4+NT)), one warp per row.
+// All rows of a warp are loaded first and their shuffle chains advance together, so the chain
+// latency is paid once per warp rather than once per row. Warp w scans rows w, w+4, w+8, ..
+// (RPW of them at most) among the first `rows`.
+template <int RPW>
+__device__ __forceinline__ void scan_rows(float *sA, int rows) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = NT / 32;
+  float4 v[RPW];
+  float tot[RPW];
+#pragma unroll
+  for (int j = 0; j < RPW; ++j) {
+    const int row = warp + j * NW;
+    v[j] = row < rows ? *(reinterpret_cast<float4 *>(sA + row * kRowStride + 4) + lane)
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
+    v[j].y += v[j].x;
+    v[j].z += v[j].y;
+    v[j].w += v[j].z;
+    tot[j] = v[j].w;
+  }
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+    for (int j = 0; j < RPW; ++j) {
+      const float o = __shfl_up_sync(0xffffffffu, tot[j], off);
+      if (lane >= off) tot[j] += o;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < RPW; ++j) {
+    const int row = warp + j * NW;
+    const float ex = tot[j] - v[j].w;
+    v[j].x += ex;
+    v[j].y += ex;
+    v[j].z += ex;
+    v[j].w += ex;
+    if (row < rows) *(reinterpret_cast<float4 *>(sA + row * kRowStride + 4) + lane) = v[j];
+  }
+}
+
+// Window sum [t, t + 2r] of a scanned shared row.
+__device__ __forceinline__ float window(const float *row, int t, int r) {
+  return row[4 + t + 2 * r] - row[3 + t];
+}
+
+// ---- bulk asynchronous copies of inverse records into shared memory (mbarrier completion)
+constexpr int kWaitLimit = 1 << 22;  // try_wait polls before a wait gives up (seconds, not cycles)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+// Thread that issues: expect `bytes` on `bar` and copy them from global `src` to shared `dst`.
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes,
+                                              uint64_t *bar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// Bounded wait for phase `parity` of `bar`; false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  for (int it = 0; it < kWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Strip-tiled inverse records (n <= 9) are staged in shared memory, a double buffer filled one
+// row ahead by bulk copies; pixel-major ones (n = 19) are loaded by phase C itself.
+template <int B>
+__host__ __device__ constexpr bool stage_records() { return records_strip_tiled(basis_n(B)); }
+
+// CTAs per SM that shared memory leaves room for when the records are staged (r = 9: three at two
+// labels per pass, two at four), passed to __launch_bounds__ as the register budget
+template <int B, int K>
+__host__ __device__ constexpr int coef_min_blocks() {
+  return !stage_records<B>() ? 1 : K <= 2 ? 3 : K <= 4 ? 2 : 1;
+}
+
+template <int B, int K, typename CT>
+__global__ void __launch_bounds__(NT, (coef_min_blocks<B, K>())) k_coef(const CT *__restrict__ cost, int H, int W, int r,
+                                             const float *__restrict__ img,
+                                             const float *__restrict__ shift,
+                                             const float *__restrict__ rec,
+                                             float *__restrict__ coef, int l_first, int n_chunk,
+                                             int band_rows, int paper_form, int *status) {
+  constexpr int NG = basis_n(B), C1 = NG + 1, NC = basis_channels_in(B), RAW = NC + K;
+  constexpr int REC = record_floats(NG), CP = coef_floats(NG);
+  constexpr bool STAGE = stage_records<B>(), kCoefReload = coef_reload(NG);
+  extern __shared__ __align__(16) float smem[];
+  // layout: 2 mbarriers | two scan buffers | two record rows | (ring)
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+  // two scan buffers used on alternate rows: a warp may start the next row's vertical update
+  // while others still read this row's window sums, so no barrier is needed at the end of a row
+  float *sA0 = smem + 4;
+  const int TW = NT - 2 * r;
+  float *recs = sA0 + 2 * K * C1 * kRowStride;      // [2][REC][TW] record rows (STAGE)
+  float *ring = recs + (STAGE ? 2 * REC * TW : 0);  // [2r+1][RAW][NT], thread-private
+  __shared__ int s_fail;
+  const int R = 2 * r + 1;
+  const size_t HW = (size_t)H * W;
+  // grid: x = label pass (fastest, so every pass over one strip and band runs back to back and
+  // they share the strip's inverse records through L2), y = strip, z = band
+  const int t = threadIdx.x;
+  const int x0 = blockIdx.y * TW;
+  const int xi = x0 - r + t;
+  const bool col_ok = xi >= 0 && xi < W;
+  const int Y0 = blockIdx.z * band_rows;
+  const int Y1 = min(H, Y0 + band_rows);
+  const int k0 = blockIdx.x * K;
+  const int nk = min(K, n_chunk - k0);
+  const int add_lo = max(0, Y0 - r);
+  const int s_begin = Y0 - r, s_end = Y1 + r;
+
+  for (int i = t; i < 2 * K * C1; i += NT) sA0[i * kRowStride + 3] = 0.f;
+  float sh[NG];
+#pragma unroll
+  for (int i = 0; i < NG; ++i) sh[i] = __ldg(shift + i);
+  // this strip's block of inverse records in row y (REC x TW floats, element-major)
+  const size_t strips = gridDim.y;
+  auto rec_block = [&](int y) { return rec + ((size_t)y * strips + blockIdx.y) * REC * TW; };
+  const uint32_t rec_bytes = (uint32_t)(REC * TW * sizeof(float));
+  auto issue_records = [&](int y) {  // thread 0 only
+    bulk_copy_g2s(recs + ((y - Y0) & 1) * REC * TW, rec_block(y), rec_bytes, &bars[(y - Y0) & 1]);
+  };
+  if (STAGE) {
+    if (t == 0) {
+      s_fail = 0;
+      mbar_init(&bars[0], 1);
+      mbar_init(&bars[1], 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (t == 0) issue_records(Y0);  // the first row has the warm-up rows to arrive
+  }
+
+  const CT *cbase = cost + (size_t)(l_first + k0) * HW;
+  auto load_row = [&](int row, float *v) {
+    if (col_ok && row >= 0 && row < H) {
+      const size_t pix = (size_t)row * W + xi;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) v[c] = __ldg(img + (size_t)c * HW + pix);
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        v[NC + k] = k < nk ? load_cost(cbase, (size_t)k * HW + pix) : 0.f;
+    }
+  };
+  float pa[RAW], pb[RAW], pc[RAW];
+  constexpr int OR = kCoefReload ? RAW : 1;  // outgoing-row buffers (reload mode only)
+  float oa[OR], ob[OR], oc[OR];
+#pragma unroll
+  for (int c = 0; c < RAW; ++c) pa[c] = pb[c] = pc[c] = 0.f;
+#pragma unroll
+  for (int c = 0; c < OR; ++c) oa[c] = ob[c] = oc[c] = 0.f;
+  auto load_old = [&](int row, float *v) {
+    if (kCoefReload && row >= add_lo) load_row(row, v);
+  };
+  load_row(s_begin, pa);
+  load_row(s_begin + 1, pb);
+  load_old(s_begin - 2 * r - 1, oa);
+  load_old(s_begin + 1 - 2 * r - 1, ob);
+
+  float V[K][C1];
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int c = 0; c < C1; ++c) V[k][c] = 0.f;
+
+  // One step per input row s: `cur` holds row s (loaded two steps earlier) and row s + 2 is
+  // loaded into `nxt`. The loop is unrolled three times so that the three buffers rotate roles
+  // without register copies (a copy would wait for the load it copies).
+  bool failed = false;
+  auto step = [&](const int s, const float *cur, float *nxt, const float *cur_o, float *nxt_o) {
+    if (s >= s_end || failed) return;
+    load_row(s + 2, nxt);
+    load_old(s + 2 - 2 * r - 1, nxt_o);
+    const int y1 = s - r;
+    const int x = x0 + t;
+    const bool coef_here = y1 >= Y0 && t < TW && x < W;
+    // ---- phase A: vertical running sums over input rows [s-2r, s]
+    if (col_ok) {
+      float *slot = ring + (size_t)(((s - s_begin) % R) * RAW) * NT + t;
+      const int so = s - 2 * r - 1;
+      if (so >= add_lo) {  // the outgoing row occupies the slot the new row will take
+        float xo[NC], go[NG];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) xo[c] = kCoefReload ? cur_o[kCoefReload ? c : 0] : slot[c * NT];
+        eval_basis<B>(xo, sh, go);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          const float p = kCoefReload ? cur_o[kCoefReload ? NC + k : 0] : slot[(NC + k) * NT];
+          V[k][0] -= p;
+#pragma unroll
+          for (int i = 0; i < NG; ++i) V[k][i + 1] = fmaf(-go[i], p, V[k][i + 1]);
+        }
+      }
+      if (s >= 0 && s < H) {
+        float g[NG];
+        eval_basis<B>(cur, sh, g);
+        if (!kCoefReload) {
+#pragma unroll
+          for (int c = 0; c < RAW; ++c) slot[c * NT] = cur[c];
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          const float p = cur[NC + k];
+          V[k][0] += p;
+#pragma unroll
+          for (int i = 0; i < NG; ++i) V[k][i + 1] = fmaf(g[i], p, V[k][i + 1]);
+        }
+      }
+    }
+    if (y1 < Y0) return;  // warm-up rows: no coefficient row complete yet (uniform per CTA)
+    float *sA = sA0 + ((y1 - Y0) & 1) * K * C1 * kRowStride;
+
+    // ---- phase B: horizontal window sums via inclusive prefix scans
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int c = 0; c < C1; ++c) sA[(k * C1 + c) * kRowStride + 4 + t] = V[k][c];
+    __syncthreads();
+    // every thread is past the previous row's phase C: the other record buffer is free
+    if (STAGE && t == 0 && y1 + 1 < Y1) issue_records(y1 + 1);
+    scan_rows<(K * C1 + NT / 32 - 1) / (NT / 32)>(sA, nk * C1);
+    if (STAGE && !mbar_wait(&bars[(y1 - Y0) & 1], ((y1 - Y0) >> 1) & 1)) s_fail = 1;
+    __syncthreads();
+    if (STAGE && s_fail) {  // a copy never completed: report, drain with a bound, stop
+      if (t == 0) {
+        atomicExch(status, 1);
+        if (y1 + 1 < Y1) mbar_wait(&bars[(y1 + 1 - Y0) & 1], ((y1 + 1 - Y0) >> 1) & 1);
+      }
+      failed = true;
+      return;
+    }
+
+    // ---- phase C: coefficients at (x, y1)
+    if (coef_here) {
+      const size_t pix = (size_t)y1 * W + x;
+      const float invN = 1.f / (float)(clipped_count(x, r, W) * clipped_count(y1, r, H));
+      const float *rrow = recs + ((y1 - Y0) & 1) * REC * TW + t;
+      int stride = TW;  // made opaque per label pair below so that addresses are not hoisted
+      auto recv = [&](int e) -> float {
+        return STAGE ? rrow[e * stride] : __ldg(rec + pix * REC + e);
+      };
+      if (paper_form) {
+        // paper form: v = Mt b~ with b~ = [B(p), B(G~_i p)], the raw window sums (no means)
+        constexpr int KP = K < 2 ? K : 2;
+#pragma unroll 1
+        for (int kb = 0; kb < K; kb += KP) {
+          if (kb >= nk) break;
+          asm volatile("" : "+r"(stride));
+          float bs[KP][C1], v[KP][C1];
+#pragma unroll
+          for (int kk = 0; kk < KP; ++kk) {
+            const float *row = sA + (kb + kk) * C1 * kRowStride;
+#pragma unroll
+            for (int c = 0; c < C1; ++c) {
+              bs[kk][c] = window(row + c * kRowStride, t, r);
+              v[kk][c] = 0.f;
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < C1; ++i) {
+#pragma unroll
+            for (int j = i; j < C1; ++j) {
+              const float Mij = recv(tri_index(C1, i, j));
+#pragma unroll
+              for (int kk = 0; kk < KP; ++kk) {
+                v[kk][i] = fmaf(Mij, bs[kk][j], v[kk][i]);
+                if (j != i) v[kk][j] = fmaf(Mij, bs[kk][i], v[kk][j]);
+              }
+            }
+          }
+#pragma unroll
+          for (int kk = 0; kk < KP; ++kk) {
+            if (kb + kk < nk) {
+              float o[CP];
+#pragma unroll
+              for (int i = 0; i < C1; ++i) o[i] = v[kk][i];
+#pragma unroll
+              for (int i = C1; i < CP; ++i) o[i] = 0.f;
+              float2 *dst =
+                  reinterpret_cast<float2 *>(coef + ((size_t)(k0 + kb + kk) * HW + pix) * CP);
+#pragma unroll
+              for (int q = 0; q < CP / 2; ++q) dst[q] = make_float2(o[2 * q], o[2 * q + 1]);
+            }
+          }
+        }
+        return;
+      }
+      float m[NG];
+#pragma unroll
+      for (int i = 0; i < NG; ++i) m[i] = recv(i);
+      // labels in pairs, one pair at a time: only two labels' cov and a are live next to the
+      // record, so four or eight labels per pass fit in registers
+      constexpr int KP = K < 2 ? K : 2;
+#pragma unroll 1
+      for (int kb = 0; kb < K; kb += KP) {
+        if (kb >= nk) break;
+        asm volatile("" : "+r"(stride));
+        float cov[KP][NG], a[KP][NG], pbar[KP];
+#pragma unroll
+        for (int kk = 0; kk < KP; ++kk) {
+          const float *row = sA + (kb + kk) * C1 * kRowStride;
+          pbar[kk] = window(row, t, r) * invN;
+#pragma unroll
+          for (int i = 0; i < NG; ++i) {
+            const float mi = window(row + (i + 1) * kRowStride, t, r) * invN;
+            cov[kk][i] = fmaf(-m[i], pbar[kk], mi);
+            a[kk][i] = 0.f;
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < NG; ++i) {
+#pragma unroll
+          for (int j = i; j < NG; ++j) {
+            const float Mij = recv(NG + tri_index(NG, i, j));
+#pragma unroll
+            for (int kk = 0; kk < KP; ++kk) {
+              a[kk][i] = fmaf(Mij, cov[kk][j], a[kk][i]);
+              if (j != i) a[kk][j] = fmaf(Mij, cov[kk][i], a[kk][j]);
+            }
+          }
+        }
+#pragma unroll
+        for (int kk = 0; kk < KP; ++kk) {
+          if (kb + kk < nk) {
+            float b = pbar[kk];
+#pragma unroll
+            for (int i = 0; i < NG; ++i) b = fmaf(-a[kk][i], m[i], b);
+            float o[CP];
+            o[0] = b;
+#pragma unroll
+            for (int i = 0; i < NG; ++i) o[i + 1] = a[kk][i];
+#pragma unroll
+            for (int i = C1; i < CP; ++i) o[i] = 0.f;
+            float2 *dst =
+                reinterpret_cast<float2 *>(coef + ((size_t)(k0 + kb + kk) * HW + pix) * CP);
+#pragma unroll
+            for (int q = 0; q < CP / 2; ++q) dst[q] = make_float2(o[2 * q], o[2 * q + 1]);
+          }
+        }
+      }
+    }
+  };
+  for (int s = s_begin; s < s_end && !failed; s += 3) {
+    step(s, pa, pc, oa, oc);
+    step(s + 1, pb, pa, ob, oa);
+    step(s + 2, pc, pb, oc, ob);
+  }
+}
+
+template <int B, bool RING>
+constexpr size_t apply_smem_bytes(int r) {
+  return sizeof(float) * ((size_t)2 * (basis_n(B) + 1) * kRowStride +
+                          (RING ? (size_t)(2 * r + 1) * (basis_n(B) + 1) * NT : 0));
+}
+
+// One label per CTA. RING: the outgoing coefficient row comes from the thread's shared-memory
+// ring; otherwise it is reloaded from device memory (used when the ring does not fit).
+template <int B, bool RING>
+__global__ void __launch_bounds__(NT) k_apply(const float *__restrict__ coef, int H, int W, int r,
+                                              const float *__restrict__ img,
+                                              const float *__restrict__ shift,
+                                              unsigned long long *__restrict__ keys,
+                                              float *__restrict__ filtered, int l_first,
+                                              int band_rows) {
+  constexpr int NG = basis_n(B), C1 = NG + 1, NC = basis_channels_in(B), CP = coef_floats(NG);
+  extern __shared__ __align__(16) float smem[];
+  float *sA0 = smem;                         // two scan buffers, alternate rows (see k_coef)
+  float *ring = smem + 2 * C1 * kRowStride;  // [2r+1][C1][NT]
+  const int R = 2 * r + 1;
+  const size_t HW = (size_t)H * W;
+  // grid: x = label (fastest), y = strip, z = band
+  const int t = threadIdx.x;
+  const int TW = NT - 2 * r;
+  const int x0 = blockIdx.y * TW;
+  const int xc = x0 - r + t;
+  const bool col_ok = xc >= 0 && xc < W;
+  const int Y0 = blockIdx.z * band_rows;
+  const int Y1 = min(H, Y0 + band_rows);
+  const int k = blockIdx.x;
+  const int add_lo = max(0, Y0 - r);
+  const int s_begin = Y0 - r, s_end = Y1 + r;
+
+  if (t < 2 * C1) sA0[t * kRowStride + 3] = 0.f;
+  float sh[NG];
+#pragma unroll
+  for (int i = 0; i < NG; ++i) sh[i] = __ldg(shift + i);
+  const float *cb = coef + (size_t)k * HW * CP;
+  auto load_row = [&](int row, float *v) {
+    if (col_ok && row >= 0 && row < H) {
+      const float2 *src = reinterpret_cast<const float2 *>(cb + ((size_t)row * W + xc) * CP);
+#pragma unroll
+      for (int q = 0; q < CP / 2; ++q) {
+        const float2 u = __ldg(src + q);
+        if (2 * q < C1) v[2 * q] = u.x;
+        if (2 * q + 1 < C1) v[2 * q + 1] = u.y;
+      }
+    }
+  };
+  // outgoing rows (only without the ring): row `row` if it entered this band's window
+  auto load_old = [&](int row, float *v) {
+    if (!RING && row >= add_lo) load_row(row, v);
+  };
+  float pa[C1], pb[C1], pc[C1];
+  float oa[RING ? 1 : C1], ob[RING ? 1 : C1], oc[RING ? 1 : C1];
+#pragma unroll
+  for (int c = 0; c < C1; ++c) pa[c] = pb[c] = pc[c] = 0.f;
+#pragma unroll
+  for (int c = 0; c < (RING ? 1 : C1); ++c) oa[c] = ob[c] = oc[c] = 0.f;
+  load_row(s_begin, pa);
+  load_row(s_begin + 1, pb);
+  load_old(s_begin - 2 * r - 1, oa);
+  load_old(s_begin + 1 - 2 * r - 1, ob);
+  float V[C1];
+#pragma unroll
+  for (int c = 0; c < C1; ++c) V[c] = 0.f;
+
+  // Same three-buffer rotation as k_coef; without the ring, the outgoing row (2r+1 rows back,
+  // resident in L2) is prefetched two steps ahead as well.
+  auto step = [&](const int s, const float *cur, float *nxt, const float *cur_o, float *nxt_o) {
+    if (s >= s_end) return;
+    load_row(s + 2, nxt);
+    if (!RING) load_old(s + 2 - 2 * r - 1, nxt_o);
+    const int y2 = s - r;
+    const int x = x0 + t;
+    const bool out_here = y2 >= Y0 && t < TW && x < W;
+    float xin[NC];
+    if (out_here) {
+      const size_t pix = (size_t)y2 * W + x;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) xin[c] = __ldg(img + (size_t)c * HW + pix);
+    }
+    if (col_ok) {
+      const int so = s - 2 * r - 1;
+      if (RING) {
+        float *slot = ring + (size_t)(((s - s_begin) % R) * C1) * NT + t;
+        if (so >= add_lo) {
+#pragma unroll
+          for (int c = 0; c < C1; ++c) V[c] -= slot[c * NT];
+        }
+        if (s >= 0 && s < H) {
+#pragma unroll
+          for (int c = 0; c < C1; ++c) {
+            V[c] += cur[c];
+            slot[c * NT] = cur[c];
+          }
+        }
+      } else {
+        if (so >= add_lo) {
+#pragma unroll
+          for (int c = 0; c < C1; ++c) V[c] -= cur_o[c];
+        }
+        if (s >= 0 && s < H) {
+#pragma unroll
+          for (int c = 0; c < C1; ++c) V[c] += cur[c];
+        }
+      }
+    }
+    if (y2 < Y0) return;
+    float *sA = sA0 + ((y2 - Y0) & 1) * C1 * kRowStride;
+
+#pragma unroll
+    for (int c = 0; c < C1; ++c) sA[c * kRowStride + 4 + t] = V[c];
+    __syncthreads();
+    scan_rows<(C1 + NT / 32 - 1) / (NT / 32)>(sA, C1);
+    __syncthreads();
+
+    if (out_here) {
+      const size_t pix = (size_t)y2 * W + x;
+      const float invN = 1.f / (float)(clipped_count(x, r, W) * clipped_count(y2, r, H));
+      float g[NG];
+      eval_basis<B>(xin, sh, g);
+      float q = window(sA, t, r);
+#pragma unroll
+      for (int i = 0; i < NG; ++i) q = fmaf(window(sA + (i + 1) * kRowStride, t, r), g[i], q);
+      q *= invN;
+      const int label = l_first + k;
+      if (filtered) filtered[(size_t)label * HW + pix] = q;
+      if (keys) atomicMin(keys + pix, wta_key(q, label));
+    }
+  };
+  for (int s = s_begin; s < s_end; s += 3) {
+    step(s, pa, pc, oa, oc);
+    step(s + 1, pb, pa, ob, oa);
+    step(s + 2, pc, pb, oc, ob);
+  }
+}
+
+
+template <typename Kern>
+cudaError_t set_smem(Kern k, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Rows per band for a kernel whose grid is strips x bands x slabs: the band count that minimises
+// (waves of resident CTAs) x (rows streamed per CTA, including the 2r warm-up rows). Callers pass
+// a nominal slab count that depends on the shape only (not on how many labels a call or chunk
+// has): the band boundaries decide the order of the running sums, so results are then identical
+// whether an image is aggregated alone, in a batch, in the serving loop or in label chunks.
+static int choose_band_rows(int H, int r, long long strips_slabs, int resident) {
+  long long best_cost = -1;
+  int best = H;
+  for (int bands = 1; bands <= std::max(1, H / std::max(8, 2 * r)); ++bands) {
+    const int rows = (H + bands - 1) / bands;
+    const long long ctas = strips_slabs * ((H + rows - 1) / rows);
+    const long long waves = (ctas + resident - 1) / resident;
+    const long long cost = waves * (rows + 2 * r);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = rows;
+    }
+  }
+  return best;
+}
+
+constexpr int kNominalLabels = 64;  // label count the band heights are planned for
+
+template <typename Kern>
+static int resident_ctas(Kern k, size_t smem) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem) != cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  return std::max(1, per_sm) * std::max(1, sms);
+}
+
+template <int B, int K>
+cudaError_t launch_chunk(const hgf_guidance *g, const void *cost, int cost_dtype, int l_first,
+                         int nc, float *filtered, float *coef_ws, unsigned long long *keys,
+                         int band_rows, bool apply_ring, int *status, cudaStream_t s,
+                         Profiler *prof) {
+  const int H = g->H, W = g->W, r = g->r;
+  const int TW = NT - 2 * r;
+  const unsigned strips = (W + TW - 1) / TW;
+  cudaError_t e;
+  {
+    const size_t sm = coef_smem(basis_n(B), basis_channels_in(B), K, r);
+    // the shared-memory limit is raised before the occupancy query so that every call (the
+    // first included) plans the same bands
+    e = set_smem(k_coef<B, K, float>, sm);
+    if (e == cudaSuccess) e = set_smem(k_coef<B, K, __nv_bfloat16>, sm);
+    if (e == cudaSuccess) e = set_smem(k_coef<B, K, __half>, sm);
+    if (e != cudaSuccess) return e;
+    const int passes = (nc + K - 1) / K;
+    // bands planned for the two-label kernel whatever K is, so that K never changes a result
+    const size_t sm2 = coef_smem(basis_n(B), basis_channels_in(B), 2, r);
+    e = set_smem(k_coef<B, 2, float>, sm2);
+    if (e != cudaSuccess) return e;
+    const int rows = band_rows > 0 ? band_rows
+                                   : choose_band_rows(H, r, (long long)strips * (kNominalLabels / 2),
+                                                      resident_ctas(k_coef<B, 2, float>, sm2));
+    dim3 grid(passes, strips, (H + rows - 1) / rows);
+    LaunchScope ls(prof, "k_coef", s);
+#define HGF_COEF(CT)                                                                          \
+  k_coef<B, K, CT><<<grid, NT, sm, s>>>((const CT *)cost, H, W, r, g->img, g->shift, g->rec,  \
+                                        coef_ws, l_first, nc, rows,                           \
+                                        g->form == HGF_FORM_PAPER ? 1 : 0, status);
+    switch (cost_dtype) {
+      case HGF_F32: HGF_COEF(float) break;
+      case HGF_BF16: HGF_COEF(__nv_bfloat16) break;
+      case HGF_F16: HGF_COEF(__half) break;
+      default: return cudaErrorInvalidValue;
+    }
+#undef HGF_COEF
+  }
+  {
+    LaunchScope ls(prof, "k_apply", s);
+    const size_t ring_sm = apply_smem_bytes<B, true>(r);
+    if (apply_ring && ring_sm <= 227 * 1024) {
+      e = set_smem(k_apply<B, true>, ring_sm);
+      if (e != cudaSuccess) return e;
+      const int rows = band_rows > 0 ? band_rows
+                                     : choose_band_rows(H, r, (long long)strips * kNominalLabels,
+                                                        resident_ctas(k_apply<B, true>, ring_sm));
+      dim3 grid(nc, strips, (H + rows - 1) / rows);
+      k_apply<B, true><<<grid, NT, ring_sm, s>>>(coef_ws, H, W, r, g->img, g->shift, keys,
+                                                 filtered, l_first, rows);
+    } else {
+      const size_t sm = apply_smem_bytes<B, false>(r);
+      e = set_smem(k_apply<B, false>, sm);
+      if (e != cudaSuccess) return e;
+      const int rows = band_rows > 0 ? band_rows
+                                     : choose_band_rows(H, r, (long long)strips * kNominalLabels,
+                                                        resident_ctas(k_apply<B, false>, sm));
+      dim3 grid(nc, strips, (H + rows - 1) / rows);
+      k_apply<B, false><<<grid, NT, sm, s>>>(coef_ws, H, W, r, g->img, g->shift, keys, filtered,
+                                             l_first, rows);
+    }
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// Every chunk of labels of one aggregation for basis B (one explicit instantiation per
+// translation unit hgf_fused_*.cu, so that the kernels compile in parallel).
+template <int B>
+cudaError_t launch_basis(const hgf_guidance *g, const void *cost, int cost_dtype, int L,
+                         float *filtered, float *coef_ws, unsigned long long *keys,
+                         const AggregatePlan &p, int *status, cudaStream_t s, Profiler *prof) {
+  cudaError_t e = cudaSuccess;
+  for (int l0 = 0; l0 < L && e == cudaSuccess; l0 += p.chunk) {
+    const int nc = std::min(p.chunk, L - l0);
+    if (p.K == 4)
+      e = launch_chunk<B, 4>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys, p.band_rows,
+                             p.apply_ring, status, s, prof);
+    else if (p.K == 8)
+      e = launch_chunk<B, 8>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys, p.band_rows,
+                             p.apply_ring, status, s, prof);
+    else
+      e = launch_chunk<B, 2>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys, p.band_rows,
+                             p.apply_ring, status, s, prof);
+  }
+  return e;
+}
+
+}  // namespace hgf
+
+#define HGF_INSTANTIATE_BASIS(B)                                                               \
+  template cudaError_t hgf::launch_basis<B>(const hgf_guidance *, const void *, int, int,      \
+                                            float *, float *, unsigned long long *,           \
+                                            const hgf::AggregatePlan &, int *, cudaStream_t,  \
+                                            hgf::Profiler *);

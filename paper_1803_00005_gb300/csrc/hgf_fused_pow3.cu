@@ -1,0 +1,4 @@
+// Fused aggregation kernels for the guidance bases B_RGB_POW3.
+#include "hgf_fused.cuh"
+
+HGF_INSTANTIATE_BASIS(hgf::B_RGB_POW3)

@@ -1,0 +1,5 @@
+// Fused aggregation kernels for the guidance bases B_RGB_MONO1, B_RGB_POW2.
+#include "hgf_fused.cuh"
+
+HGF_INSTANTIATE_BASIS(hgf::B_RGB_MONO1)
+HGF_INSTANTIATE_BASIS(hgf::B_RGB_POW2)

@@ -31,10 +31,37 @@ bool make_basis_table(int C, int degree, int basis, BasisTable *t);
 
 inline int packed_size(int n) { return n * (n + 1) / 2; }
 
-// Per-pixel record of the resident inverse used by the fused kernels: [mu_0..mu_{n-1} |
-// packed Minv | padding], a multiple of 4 floats so that records are 16-byte aligned.
+// Per-pixel record of the resident inverse used by the fused kernels, a multiple of 4 floats so
+// that records are 16-byte aligned. Centred form: [mu_0..mu_{n-1} | packed n x n Minv | pad];
+// paper form: [packed (n+1) x (n+1) inverse | pad], one float more, hence the + 1.
 __host__ __device__ constexpr int record_floats(int n) {
-  return (n + n * (n + 1) / 2 + 3) / 4 * 4;
+  return (n + n * (n + 1) / 2 + 1 + 3) / 4 * 4;
+}
+// Records of up to 68 floats (n <= 9) are stored strip by strip, in the order the fused
+// coefficient kernel stages them in shared memory: strip s of image row y covers columns
+// [s*TW, s*TW + TW) with TW = record_strip_width(r) (the strip width of the fused kernels), and
+// holds record_floats(n) x TW floats element-major (element e of the strip's j-th pixel at
+// e*TW + j). One strip row is one contiguous, 16-byte aligned block; the columns of the last strip
+// past W are padding. Larger records (n = 19) stay pixel-major: H x W x record_floats(n).
+__host__ __device__ constexpr bool records_strip_tiled(int n) { return record_floats(n) <= 68; }
+__host__ __device__ constexpr int record_strip_width(int r) {
+  return kStripThreads - 2 * r > 1 ? kStripThreads - 2 * r : 1;
+}
+inline size_t record_total_floats(int H, int W, int n, int r) {
+  if (!records_strip_tiled(n)) return (size_t)H * W * record_floats(n);
+  const size_t tw = (size_t)record_strip_width(r);
+  return (size_t)H * ((W + tw - 1) / tw) * tw * record_floats(n);
+}
+
+#ifndef HGF_COEF_RELOAD
+#define HGF_COEF_RELOAD -1
+#endif
+// k_coef gets the input row leaving its vertical window either from a per-thread shared-memory
+// ring or by re-reading it from device memory, where it is still cached in L2, prefetched two
+// rows ahead like the new rows. Reload where the records are staged (their buffers take the
+// ring's shared memory), the ring otherwise; HGF_COEF_RELOAD = 0 or 1 forces one of them.
+__host__ __device__ constexpr bool coef_reload(int n) {
+  return HGF_COEF_RELOAD < 0 ? records_strip_tiled(n) : HGF_COEF_RELOAD != 0;
 }
 // Per-pixel coefficient record of the fused kernels' workspace: [b, a_1..a_n | padding] rounded
 // up to an even count so that it is read and written as float2 pairs.
@@ -155,12 +182,12 @@ struct hgf_guidance {
   hgf_ctx *ctx = nullptr;
   int C = 0, H = 0, W = 0, n = 0, degree = 0, basis = 0, r = 0;
   double eps = 0.0;
-  int inv_precision = HGF_F64, combine = HGF_COMBINE_ALPHA;
+  int inv_precision = HGF_F64, combine = HGF_COMBINE_ALPHA, form = HGF_FORM_CENTRED;
   float *img = nullptr;    // C x H x W, copy of the input image
   float *G = nullptr;      // n x H x W, shifted guidance G_i - c_i
-  float *minv = nullptr;   // n(n+1)/2 x H x W, packed (Sigma + eps E)^-1
-  float *mu = nullptr;     // n x H x W, shifted means A(G_i) - c_i
-  float *rec = nullptr;    // H x W x record_floats(n): [mu | packed Minv] per pixel
+  float *minv = nullptr;   // n(n+1)/2 x H x W, packed (Sigma + eps E)^-1 (centred form only)
+  float *mu = nullptr;     // n x H x W, shifted means A(G_i) - c_i (centred form only)
+  float *rec = nullptr;    // [mu | packed Minv] per pixel (layout: records_strip_tiled)
   float *shift = nullptr;  // n, device: c_i (image mean of G_i)
 };
 
@@ -197,6 +224,19 @@ bool aggregate_supported(int n);
 hgf_status alloc_guidance_checked(hgf_ctx *ctx, int C, int H, int W, const hgf_params *p,
                                   hgf_guidance **out);
 void free_guidance(hgf_guidance *g);
-bool aggregate_fits(const hgf_guidance *g);  // fused kernels take this shape
+bool aggregate_fits(const hgf_guidance *g);
+// Batched (lambda E + S_i)^-1, packed, element-major over the batch (hgf_batched_inverse).
+cudaError_t launch_batched_inverse(const double *S, int count, int n, double lambda, int method,
+                                   int precision, double *out, cudaStream_t s, Profiler *prof);
+// Dynamic shared memory of k_coef for n guidance channels, C input channels, K labels, radius r.
+size_t coef_smem(int n, int C, int K, int r);
+// Device address of the current device's watchdog word (hgf_device_status).
+int *device_status_ptr();
+template <int B>
+cudaError_t launch_basis(const hgf_guidance *g, const void *cost, int cost_dtype, int L,
+                         float *filtered, float *coef_ws, unsigned long long *keys,
+                         const AggregatePlan &p, int *status, cudaStream_t s, Profiler *prof);
+// Reads (and, with clear, resets) the current device's watchdog word set by bounded waits.
+cudaError_t read_device_status(int *status, bool clear);  // fused kernels take this shape
 
 }  // namespace hgf

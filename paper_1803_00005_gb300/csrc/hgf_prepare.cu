@@ -8,6 +8,7 @@
 // sums of 2r+1 terms per axis; the assembly Sigma = A(GG^T) - mu mu^T and the recursion run in the
 // precision chosen by hgf_params.inv_precision (float64 by default).
 #include "hgf_basis.cuh"
+#include "hgf_prop1.cuh"
 
 #include <algorithm>
 
@@ -192,14 +193,29 @@ __global__ void k_moment_cols(const float *__restrict__ rows, int H, int W, int 
 }
 
 // ------------------------------------------------------------------- assembly + HGF inverse
-// One thread per pixel. Dividing the window sums of the moments by N gives the means
-// mu_i = A(G_i) and E_ij = A(G_i G_j). Then S = E - mu mu^T (Sec. 5.1) and Prop. 1 with
-// lambda = eps: for kappa = 0..n-1 (starting from an empty alpha)
-//   u_i   = sum_{j<kappa} alpha_ij S_{j kappa}
-//   gamma = -1 / (1 + S_{kappa kappa} / lambda + sum_{i<kappa} S_{kappa i} u_i)
-//   alpha_ij += gamma u_i u_j (i, j < kappa);  alpha_{i kappa} = gamma u_i / lambda;
-//   alpha_{kappa kappa} = gamma / lambda^2
-// which yields (lambda E + S)^-1 = lambda^-1 E + S alpha (Eq. HGF_w3) = -lambda alpha.
+// Writes one pixel's record in the layout records_strip_tiled(NG) selects.
+template <int NG>
+__device__ __forceinline__ void store_record(float *rec, const float *out, int x, int y, int W,
+                                             int r) {
+  constexpr int REC = record_floats(NG);
+  if (records_strip_tiled(NG)) {
+    // strip-tiled, element-major record (consecutive threads write consecutive addresses)
+    const int tw = record_strip_width(r);
+    const int strip = x / tw;
+    float *dst = rec + ((size_t)y * ((W + tw - 1) / tw) + strip) * REC * tw + (x - strip * tw);
+#pragma unroll
+    for (int e = 0; e < REC; ++e) dst[(size_t)e * tw] = out[e];
+  } else {
+    float4 *dst = reinterpret_cast<float4 *>(rec + ((size_t)y * W + x) * REC);
+#pragma unroll
+    for (int q = 0; q < REC / 4; ++q)
+      dst[q] = make_float4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
+  }
+}
+
+// Centred form, one thread per pixel. Dividing the window sums of the (shifted) moments by N
+// gives the means mu_i = A(G_i) and E_ij = A(G_i G_j); S = E - mu mu^T (Sec. 5.1), Prop. 1 with
+// lambda = eps. Record: [mu | packed (S + eps E)^-1 | 0].
 template <int NG, typename T>
 __global__ void __launch_bounds__(128) k_inverse(const float *__restrict__ mom, int H, int W,
                                                  int r, double eps, int combine,
@@ -233,64 +249,103 @@ __global__ void __launch_bounds__(128) k_inverse(const float *__restrict__ mom, 
   const T lam = T(eps);
   const T inv_lam = T(1) / lam;
   T al[P];
-#pragma unroll
-  for (int e = 0; e < P; ++e) al[e] = T(0);
-#pragma unroll
-  for (int k = 0; k < NG; ++k) {
-    T u[NG > 1 ? NG - 1 : 1];
-#pragma unroll
-    for (int i = 0; i < k; ++i) {
-      T acc = T(0);
-#pragma unroll
-      for (int j = 0; j < k; ++j)
-        acc = fma(al[tri_index(NG, i < j ? i : j, i < j ? j : i)], S[tri_index(NG, j, k)], acc);
-      u[i] = acc;
-    }
-    T den = T(1) + S[tri_index(NG, k, k)] * inv_lam;
-#pragma unroll
-    for (int i = 0; i < k; ++i) den = fma(S[tri_index(NG, i, k)], u[i], den);
-    const T gam = T(-1) / den;
-#pragma unroll
-    for (int i = 0; i < k; ++i) {
-      const T v = gam * u[i];
-#pragma unroll
-      for (int j = i; j < k; ++j) al[tri_index(NG, i, j)] = fma(v, u[j], al[tri_index(NG, i, j)]);
-      al[tri_index(NG, i, k)] = v * inv_lam;
-    }
-    al[tri_index(NG, k, k)] = gam * inv_lam * inv_lam;
-  }
+  prop1_alpha<NG, T>(S, inv_lam, al);
 
   constexpr int REC = record_floats(NG);
   float out[REC];
 #pragma unroll
   for (int i = 0; i < NG; ++i) out[i] = (float)m[i];
-  if (combine == HGF_COMBINE_W3) {
 #pragma unroll
-    for (int i = 0; i < NG; ++i) {
+  for (int i = 0; i < NG; ++i)
 #pragma unroll
-      for (int j = i; j < NG; ++j) {
-        T acc = (i == j) ? inv_lam : T(0);
-#pragma unroll
-        for (int k = 0; k < NG; ++k)
-          acc = fma(S[tri_index(NG, i < k ? i : k, i < k ? k : i)],
-                    al[tri_index(NG, k < j ? k : j, k < j ? j : k)], acc);
-        out[NG + tri_index(NG, i, j)] = (float)acc;
-      }
-    }
-  } else {
-#pragma unroll
-    for (int e = 0; e < P; ++e) out[NG + e] = (float)(-lam * al[e]);
-  }
+    for (int j = i; j < NG; ++j)
+      out[NG + tri_index(NG, i, j)] =
+          (float)inverse_entry<NG, T>(S, al, lam, inv_lam, combine, i, j);
 #pragma unroll
   for (int e = NG + P; e < REC; ++e) out[e] = 0.f;
 #pragma unroll
   for (int e = 0; e < P; ++e) minv[(size_t)e * HW + pix] = out[NG + e];
 #pragma unroll
   for (int i = 0; i < NG; ++i) mu[(size_t)i * HW + pix] = out[i];
-  float4 *dst = reinterpret_cast<float4 *>(rec + pix * REC);
+  store_record<NG>(rec, out, x, y, W, r);
+}
+
+// Paper form (Secs. 3-4), one thread per pixel: G_0 = 1 joins the guidance and the uncentred
+// (n+1) x (n+1) Gram matrix of window sums, Gram_ij = B(G_i G_j), is inverted with lambda = eps
+// in sum units by Prop. 1. The moments are window sums of the shifted channels G~_i = G_i - c_i,
+// so Gram = T Gram~ T^T with [1, G] = T [1, G~], T = [[1, 0], [c, E]], rebuilt here in FP64. The
+// record holds Mt = T^T (lambda E + Gram)^-1 T, packed: the fused kernels multiply it by the
+// shifted slice sums b~ = B([1, G~] p) = T^-1 b, which gives v = T^T w, and the output
+// sum_i A(w_i) G_i + A(w_0) equals A(v_0) + sum_i A(v_i) G~_i: the same coefficient layout
+// [v_0 | v_1..v_n] as the centred form's [b | a].
+template <int NG, typename T>
+__global__ void __launch_bounds__(128) k_inverse_paper(const float *__restrict__ mom, int H,
+                                                       int W, int r, double eps, int combine,
+                                                       const float *__restrict__ shift,
+                                                       float *__restrict__ rec) {
+  constexpr int P = NG * (NG + 1) / 2, M = NG + 1, PM = M * (M + 1) / 2;
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y;
+  if (x >= W) return;
+  size_t HW = (size_t)H * W;
+  size_t pix = (size_t)y * W + x;
+  const T N = T(clipped_count(x, r, W) * clipped_count(y, r, H));
+
+  T c[NG], sg[NG];
 #pragma unroll
-  for (int q = 0; q < REC / 4; ++q)
-    dst[q] = make_float4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
+  for (int i = 0; i < NG; ++i) {
+    c[i] = T(__ldg(shift + i));
+    sg[i] = T(__ldg(mom + (size_t)i * HW + pix));
+  }
+  T S[PM];
+  S[tri_index(M, 0, 0)] = N;
+#pragma unroll
+  for (int i = 0; i < NG; ++i) S[tri_index(M, 0, i + 1)] = fma(c[i], N, sg[i]);
+#pragma unroll
+  for (int i = 0; i < NG; ++i) {
+#pragma unroll
+    for (int j = i; j < NG; ++j) {
+      const T sgg = T(__ldg(mom + (size_t)(NG + tri_index(NG, i, j)) * HW + pix));
+      S[tri_index(M, i + 1, j + 1)] = sgg + c[i] * sg[j] + c[j] * sg[i] + c[i] * c[j] * N;
+    }
+  }
+
+  const T lam = T(eps);
+  const T inv_lam = T(1) / lam;
+  T al[PM];
+  prop1_alpha<M, T>(S, inv_lam, al);
+  // Q = (lambda E + Gram)^-1 (packed, in al's place), then Mt = T^T Q T
+  T Q[PM];
+#pragma unroll
+  for (int i = 0; i < M; ++i)
+#pragma unroll
+    for (int j = i; j < M; ++j)
+      Q[tri_index(M, i, j)] = inverse_entry<M, T>(S, al, lam, inv_lam, combine, i, j);
+  auto q = [&](int i, int j) { return Q[tri_index(M, i < j ? i : j, i < j ? j : i)]; };
+  T u[M];  // u_j = (Q T)_{j0} = Q_j0 + sum_{l>=1} Q_jl c_l
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    T acc = q(j, 0);
+#pragma unroll
+    for (int l = 1; l < M; ++l) acc = fma(q(j, l), c[l - 1], acc);
+    u[j] = acc;
+  }
+  constexpr int REC = record_floats(NG);
+  float out[REC];
+  T m00 = u[0];
+#pragma unroll
+  for (int j = 1; j < M; ++j) m00 = fma(c[j - 1], u[j], m00);
+  out[tri_index(M, 0, 0)] = (float)m00;
+#pragma unroll
+  for (int k = 1; k < M; ++k) out[tri_index(M, 0, k)] = (float)u[k];  // (T^T Q T)_{0k} = u_k
+#pragma unroll
+  for (int i = 1; i < M; ++i)
+#pragma unroll
+    for (int k = i; k < M; ++k) out[tri_index(M, i, k)] = (float)q(i, k);
+#pragma unroll
+  for (int e = PM; e < REC; ++e) out[e] = 0.f;
+  store_record<NG>(rec, out, x, y, W, r);
+  (void)P;
 }
 
 template <int NG, typename T>
@@ -298,8 +353,12 @@ static void launch_inverse_t(const float *mom, const hgf_guidance *g, cudaStream
                              Profiler *prof) {
   dim3 grid((g->W + 127) / 128, g->H);
   LaunchScope ls(prof, "k_inverse", s);
-  k_inverse<NG, T><<<grid, 128, 0, s>>>(mom, g->H, g->W, g->r, g->eps, g->combine, g->minv,
-                                         g->mu, g->rec);
+  if (g->form == HGF_FORM_PAPER)
+    k_inverse_paper<NG, T><<<grid, 128, 0, s>>>(mom, g->H, g->W, g->r, g->eps, g->combine,
+                                                 g->shift, g->rec);
+  else
+    k_inverse<NG, T><<<grid, 128, 0, s>>>(mom, g->H, g->W, g->r, g->eps, g->combine, g->minv,
+                                           g->mu, g->rec);
 }
 
 template <typename T>

@@ -35,11 +35,12 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
 
 struct CacheKey {
   uint64_t key;
-  int C, H, W, degree, basis, r, prec, combine;
+  int C, H, W, degree, basis, r, prec, combine, form;
   double eps;
   bool operator<(const CacheKey &o) const {
-    return std::tie(key, C, H, W, degree, basis, r, prec, combine, eps) <
-           std::tie(o.key, o.C, o.H, o.W, o.degree, o.basis, o.r, o.prec, o.combine, o.eps);
+    return std::tie(key, C, H, W, degree, basis, r, prec, combine, form, eps) <
+           std::tie(o.key, o.C, o.H, o.W, o.degree, o.basis, o.r, o.prec, o.combine, o.form,
+                    o.eps);
   }
 };
 
@@ -75,9 +76,10 @@ struct Slot {
   Req *req = nullptr;
 };
 
-size_t guidance_bytes_for(int C, int H, int W, int n) {
+size_t guidance_bytes_for(int C, int H, int W, int n, int r) {
   const size_t HW = (size_t)H * W;
-  return (HW * ((size_t)record_floats(n) + C + n + packed_size(n) + n) + 64) * sizeof(float);
+  return (HW * ((size_t)C + n + packed_size(n) + n) + record_total_floats(H, W, n, r) + 64) *
+         sizeof(float);
 }
 
 }  // namespace
@@ -145,7 +147,7 @@ struct hgf_server {
     Slot &sl = slots[si];
     const hgf_request &r = q->r;
     CacheKey key{r.guidance_key, r.C, r.H, r.W, r.params.degree, r.params.basis, r.params.r,
-                 r.params.inv_precision, r.params.combine, r.params.eps};
+                 r.params.inv_precision, r.params.combine, r.params.form, r.params.eps};
     auto it = cache.find(key);
     CacheEntry *e = nullptr;
     cudaError_t err = cudaSuccess;
@@ -187,9 +189,10 @@ struct hgf_server {
       g.eps = r.params.eps;
       g.inv_precision = r.params.inv_precision;
       g.combine = r.params.combine;
+      g.form = r.params.form;
       const size_t HW = (size_t)r.H * r.W;
       g.rec = (float *)ent->base;
-      g.img = g.rec + (size_t)record_floats(g.n) * HW;
+      g.img = g.rec + record_total_floats(r.H, r.W, g.n, g.r);
       g.G = g.img + (size_t)g.C * HW;
       g.minv = g.G + (size_t)g.n * HW;
       g.mu = g.minv + (size_t)packed_size(g.n) * HW;
@@ -345,7 +348,8 @@ hgf_status hgf_serve_submit(hgf_server *s, const hgf_request *req, uint64_t *id)
       (r.C != 1 && r.C != 3) || r.params.r < 0 || !(r.params.eps > 0.0) ||
       (r.cost_dtype != HGF_F32 && r.cost_dtype != HGF_BF16 && r.cost_dtype != HGF_F16) ||
       (r.params.inv_precision != HGF_F64 && r.params.inv_precision != HGF_F32) ||
-      (r.params.combine != HGF_COMBINE_ALPHA && r.params.combine != HGF_COMBINE_W3))
+      (r.params.combine != HGF_COMBINE_ALPHA && r.params.combine != HGF_COMBINE_W3) ||
+      (r.params.form != HGF_FORM_CENTRED && r.params.form != HGF_FORM_PAPER))
     return HGF_EINVAL;
   const int n = hgf_num_channels(r.C, r.params.degree, r.params.basis);
   if (n < 1 || !aggregate_supported(n)) return HGF_EUNSUPPORTED;
@@ -360,7 +364,7 @@ hgf_status hgf_serve_submit(hgf_server *s, const hgf_request *req, uint64_t *id)
     ++s->rejected_nomem;
     return HGF_EUNSUPPORTED;
   }
-  const size_t gb = guidance_bytes_for(r.C, r.H, r.W, n);
+  const size_t gb = guidance_bytes_for(r.C, r.H, r.W, n, probe.r);
   if (s->slot_bytes + gb > s->budget) {
     ++s->rejected_nomem;
     return HGF_ENOMEM;

@@ -20,9 +20,12 @@ STATUS_NAMES = ["HGF_OK", "HGF_EINVAL", "HGF_ENOMEM", "HGF_ECUDA", "HGF_ETIMEOUT
 HGF_F32, HGF_BF16, HGF_F16, HGF_F64 = range(4)
 HGF_BASIS_MONOMIAL, HGF_BASIS_POWERS = range(2)
 HGF_COMBINE_ALPHA, HGF_COMBINE_W3 = range(2)
+HGF_FORM_CENTRED, HGF_FORM_PAPER = range(2)
+HGF_INV_PROP1, HGF_INV_CHOLESKY = range(2)
 
 DTYPE_CODES = {"f32": HGF_F32, "bf16": HGF_BF16, "f16": HGF_F16, "f64": HGF_F64}
 BASIS_CODES = {"monomial": HGF_BASIS_MONOMIAL, "powers": HGF_BASIS_POWERS}
+FORM_CODES = {"centred": HGF_FORM_CENTRED, "paper": HGF_FORM_PAPER}
 
 # Every symbol include/hgf.h declares.
 EXPORTED = [
@@ -33,6 +36,7 @@ EXPORTED = [
     "hgf_aggregate_static", "hgf_serve_create", "hgf_serve_submit", "hgf_serve_poll",
     "hgf_serve_wait", "hgf_serve_stats", "hgf_serve_inject_alloc_failures", "hgf_serve_destroy",
     "hgf_batch_create", "hgf_batch_run", "hgf_batch_launch_graph", "hgf_batch_destroy",
+    "hgf_device_status", "hgf_batched_inverse",
 ]
 
 
@@ -46,7 +50,7 @@ class HGFError(RuntimeError):
 class hgf_params(ctypes.Structure):
     _fields_ = [("degree", ctypes.c_int), ("basis", ctypes.c_int), ("r", ctypes.c_int),
                 ("eps", ctypes.c_double), ("inv_precision", ctypes.c_int),
-                ("combine", ctypes.c_int)]
+                ("combine", ctypes.c_int), ("form", ctypes.c_int)]
 
 
 class hgf_tuning(ctypes.Structure):
@@ -126,6 +130,8 @@ def lib():
         "hgf_set_tuning": (c_int, [vp, P(hgf_tuning)]),
         "hgf_guidance_update": (c_int, [vp, vp, vp, vp]),
         "hgf_launch_count": (c_int, [vp, P(ctypes.c_ulonglong)]),
+        "hgf_device_status": (c_int, [vp, P(c_int), c_int]),
+        "hgf_batched_inverse": (c_int, [vp, vp, c_int, c_int, c_double, c_int, c_int, vp, vp]),
         "hgf_profile_enable": (c_int, [vp, c_int]),
         "hgf_profile_report": (c_int, [vp, ctypes.c_char_p, ctypes.c_size_t]),
     }
@@ -167,10 +173,14 @@ def _require_cuda(t, name):
         raise ValueError(f"{name} must be a contiguous CUDA tensor")
 
 
-def make_params(degree=1, r=4, eps=1e-4, basis="monomial", inv_precision="f64", combine="alpha"):
+def make_params(degree=1, r=4, eps=1e-4, basis="monomial", inv_precision="f64", combine="alpha",
+                form="centred"):
+    """form: "centred" (Sec. 5.1; eps in units of window means) or "paper" (G_0 = 1, uncentred
+    window sums, lambda = eps in units of window sums; Sec. 3-4)."""
     return hgf_params(degree=int(degree), basis=BASIS_CODES[basis], r=int(r), eps=float(eps),
                       inv_precision=DTYPE_CODES[inv_precision],
-                      combine=HGF_COMBINE_ALPHA if combine == "alpha" else HGF_COMBINE_W3)
+                      combine=HGF_COMBINE_ALPHA if combine == "alpha" else HGF_COMBINE_W3,
+                      form=FORM_CODES[form])
 
 
 # ------------------------------------------------------------------ entry points, same names
@@ -303,6 +313,32 @@ def hgf_guidance_update(ctx, g, img, stream=None):
 def hgf_launch_count(ctx):
     v = ctypes.c_ulonglong()
     _check(ctx, lib().hgf_launch_count(ctx, ctypes.byref(v)))
+    return v.value
+
+
+def hgf_batched_inverse(ctx, S, n, lam, method="prop1", precision="f64", out=None, stream=None):
+    """(lam E + S_i)^-1 for the packed, element-major float64 batch S of shape (n(n+1)/2, count)
+    on the device; returns `out` (allocated like S when None)."""
+    _require_cuda(S, "S")
+    if S.dim() != 2 or S.shape[0] != n * (n + 1) // 2 or str(S.dtype) != "torch.float64":
+        raise ValueError("S must be float64 of shape (n(n+1)/2, count)")
+    if out is None:
+        import torch
+        out = torch.empty_like(S)
+    _require_cuda(out, "out")
+    count = int(S.shape[1])
+    _check(ctx, lib().hgf_batched_inverse(
+        ctx, _ptr(S), count, int(n), float(lam),
+        HGF_INV_PROP1 if method == "prop1" else HGF_INV_CHOLESKY, DTYPE_CODES[precision],
+        _ptr(out), _stream(stream)))
+    return out
+
+
+def hgf_device_status(ctx, clear=False):
+    """Watchdog word of ctx's device after all its work: 0 unless a bounded wait in a kernel ran
+    out (that call's results are then incomplete)."""
+    v = ctypes.c_int()
+    _check(ctx, lib().hgf_device_status(ctx, ctypes.byref(v), 1 if clear else 0))
     return v.value
 
 

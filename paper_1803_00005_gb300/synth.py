@@ -19,7 +19,8 @@ import numpy as np
 __all__ = [
     "StereoCase", "stereo_pair", "cost_volume", "cost_volume_torch", "make_case", "to_dtype",
     "CONFIG_SMALL",
-    "CONFIG_QUARTER", "CONFIG_LARGE", "batched_cases", "serving_requests",
+    "CONFIG_QUARTER", "CONFIG_LARGE", "batched_cases", "serving_requests", "gram_batch",
+    "gram_batch_torch", "pack_upper",
 ]
 
 
@@ -226,3 +227,34 @@ def serving_requests(n_requests: int, rate_hz: float = 200.0, seed: int = 5, reu
                         guidance_key=i, image_seed=5000 + i, reused=False)
         reqs.append(spec)
     return reqs
+
+
+def gram_batch(count: int, n: int, samples: int = 25, seed: int = 7) -> np.ndarray:
+    """count Gram matrices S_i = sum_k x_k x_k^T of `samples` guidance vectors x_k ~ U[0,1]^n each
+    (a window's worth of polynomial-guidance samples, the matrices Sec. 3's recursion inverts);
+    float64, shape (count, n, n)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    X = rng.uniform(0.0, 1.0, size=(count, samples, n))
+    return np.einsum("cki,ckj->cij", X, X)
+
+
+def gram_batch_torch(count: int, n: int, samples: int = 25, seed: int = 7, device="cuda"):
+    """Same recipe built on the device with torch (for large batches): float64 (count, n, n)."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    X = torch.rand((count, samples, n), generator=gen, dtype=torch.float64, device=device)
+    return torch.bmm(X.transpose(1, 2), X)
+
+
+def pack_upper(S):
+    """(count, n, n) -> packed upper triangles row by row, element-major: (n(n+1)/2, count).
+    Works for numpy arrays and torch tensors."""
+    n = S.shape[-1]
+    rows, cols = np.triu_indices(n)
+    if isinstance(S, np.ndarray):
+        return S[:, rows, cols].T.copy()
+    import torch
+    r = torch.as_tensor(rows, device=S.device)
+    c = torch.as_tensor(cols, device=S.device)
+    return S[:, r, c].transpose(0, 1).contiguous()
