@@ -107,7 +107,72 @@ def parse():
     ap.add_argument("--batch", action="store_true",
                     help="32 mixed-size stereo pairs as one batch, one captured graph per step")
     ap.add_argument("--streams", type=int, default=8, help="batch: internal streams")
+    ap.add_argument("--inverse", action="store_true",
+                    help="batched-inverse microbenchmark: Prop. 1 vs per-matrix Cholesky")
+    ap.add_argument("--count", type=int, default=1_000_000, help="inverse: matrices per batch")
     return ap.parse_args()
+
+
+def inverse_arm(args):
+    """Batched (lambda E + S_i)^-1 of 10^6 seeded Gram matrices (25 samples of U[0,1]^n each,
+    lambda = 0.05), n = 3, 6, 9, 19: Prop. 1's recursion against per-matrix Cholesky, float64 and
+    float32 arithmetic, one thread per matrix (Sec. 3, Fig. 1b). A 256 MiB buffer is written
+    between timed launches to flush L2. value = Prop. 1, float64, n = 9, matrices/s."""
+    import torch
+    from paper_1803_00005_gb300 import build, hgf, synth
+    build.build()
+    torch.cuda.set_device(0)
+    ctx = hgf.hgf_create(0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    reps = max(3, min(args.steps, 20))
+    table = []
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = hgf.hgf_launch_count(ctx)
+    for n in (3, 6, 9, 19):
+        S = synth.pack_upper(synth.gram_batch_torch(args.count, n, seed=11 + n))
+        out = torch.empty_like(S)
+        for method in ("prop1", "cholesky"):
+            for prec in ("f64", "f32"):
+                for _ in range(max(3, args.warmup)):
+                    hgf.hgf_batched_inverse(ctx, S, n, 0.05, method, prec, out)
+                ms = []
+                for i in range(reps):
+                    flush.fill_(i & 0xff)
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    hgf.hgf_batched_inverse(ctx, S, n, 0.05, method, prec, out)
+                    b.record(stream)
+                    b.synchronize()
+                    ms.append(a.elapsed_time(b))
+                t = statistics.median(ms) / 1e3
+                P = n * (n + 1) // 2
+                table.append(dict(n=n, method=method, precision=prec,
+                                  matrices_per_s=args.count / t, ms=1e3 * t,
+                                  gbs=2 * P * 8 * args.count / t / 1e9))
+        del S, out
+    clk = clocks.stop()
+    launches = hgf.hgf_launch_count(ctx) - launches0
+    hgf.hgf_destroy(ctx)
+    key = next(r for r in table if r["n"] == 9 and r["method"] == "prop1" and
+               r["precision"] == "f64")
+    ratio = {f"n={n} {prec}": next(r["ms"] for r in table if r["n"] == n and
+                                   r["method"] == "cholesky" and r["precision"] == prec) /
+             next(r["ms"] for r in table if r["n"] == n and r["method"] == "prop1" and
+                  r["precision"] == prec)
+             for n in (3, 6, 9, 19) for prec in ("f64", "f32")}
+    line = dict(metric="matrices/s, batched (lambda E + S)^-1, Prop. 1, n=9, float64",
+                value=key["matrices_per_s"], unit="matrices/s", n_gpus=1, steps=reps,
+                warmup=max(3, args.warmup), ms_per_step=key["ms"], higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic", impl="inverse",
+                config=dict(workload=f"{args.count} Gram matrices of 25 U[0,1]^n samples, "
+                                     "lambda=0.05, packed float64 in and out",
+                            l2="256 MiB flush between launches"),
+                table=table, cholesky_over_prop1_time=ratio, gpu_launches=launches,
+                clocks=clk)
+    print(json.dumps(line), flush=True)
 
 
 def batch_arm(args):
@@ -337,6 +402,8 @@ def main():
         return serve_arm(args)
     if args.batch:
         return batch_arm(args)
+    if args.inverse:
+        return inverse_arm(args)
     if args.impl == "reference":
         return reference_arm(args, w)
 
@@ -465,6 +532,39 @@ def main():
                                           pin_cost.element_size()),
                    d2h_bytes_per_step=int(H * W * 4))
 
+    # end to end from the stereo pair itself: both views uploaded from pinned host memory, the
+    # cost computed inside the coefficient kernel (hgf_aggregate_stereo), labels read back
+    e2e_stereo = None
+    if not args.no_e2e and args.impl == "fused":
+        left, right, _ = synth.stereo_pair(W, H, L, w["seed"])
+        pin_l = torch.from_numpy(left.astype(np.float32)).pin_memory()
+        pin_r = torch.from_numpy(right.astype(np.float32)).pin_memory()
+        pin_lab = torch.empty((H, W), dtype=torch.int32).pin_memory()
+        dl = torch.empty_like(pin_l, device=dev)
+        dr = torch.empty_like(pin_r, device=dev)
+
+        def stereo_step():
+            dl.copy_(pin_l, non_blocking=True)
+            dr.copy_(pin_r, non_blocking=True)
+            hgf.hgf_guidance_update(ctx, g, dl)
+            hgf.hgf_aggregate_stereo(ctx, g, dr, L, labels=labels)
+            pin_lab.copy_(labels, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+
+        for _ in range(3):
+            stereo_step()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            stereo_step()
+        ts = time.perf_counter() - t0
+        if world > 1:
+            ts = world_max(ts, dist, dev)
+        e2e_stereo = dict(value=whole_job_value(units, world, ts), unit=UNIT,
+                          h2d_bytes_per_step=int(2 * pin_l.numel() * 4),
+                          d2h_bytes_per_step=int(H * W * 4),
+                          note="stereo pair in, labels out; cost computed on the device "
+                               "(truncated colour + gradient, inside the coefficient kernel)")
+
     hgf.hgf_guidance_release(g)
     hgf.hgf_destroy(ctx)
     if rank == 0:
@@ -476,7 +576,8 @@ def main():
                     config=dict(workload=w["name"], parallelism=f"replicas x{world}",
                                 l2="256 MiB buffer written between timed steps",
                                 step="guidance precompute + aggregate + WTA"),
-                    roofline=roof, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches),
+                    roofline=roof, cpu_baseline=cpu, e2e=e2e, e2e_stereo=e2e_stereo,
+                    gpu_launches=int(launches),
                     clocks=clk, kernels=kernels, wall_s=wall,
                     step_ms=dict(min=min(step_ms), median=statistics.median(step_ms)))
         print(json.dumps(line), flush=True)

@@ -178,6 +178,17 @@ typedef struct {
   int apply_mode;
 } hgf_tuning;
 hgf_status hgf_set_tuning(hgf_ctx *ctx, const hgf_tuning *t);
+/* Autotuner (no counterpart in the paper): times hgf_aggregate on (g, cost) under every tuning
+ * that leaves the results bit-identical - labels per pass 2, 4 or 8 (where shared memory allows),
+ * labels per chunk (all, 64, 16) and the output kernel's outgoing-row source (reload, ring) -
+ * with the row bands of the automatic plan (bands change rounding, so they are not tuned). Each
+ * candidate runs once untimed, then `reps` times between CUDA events on `stream`. The fastest
+ * becomes ctx's tuning and is written to *best (may be NULL); *ncand (may be NULL) receives the
+ * number of candidates timed. labels: device int32 H x W, scratch output. Blocks until done.
+ * HGF_EINVAL on bad arguments or reps < 1; errors of hgf_aggregate otherwise. */
+hgf_status hgf_autotune(hgf_ctx *ctx, const hgf_guidance *g, const void *cost, int cost_dtype,
+                        int L, int32_t *labels, int reps, hgf_tuning *best, int *ncand,
+                        void *stream);
 
 /* ---------------------------------------------------------------------------------------------
  * Batches (no counterpart in the paper): many images of different sizes, label counts and
@@ -261,6 +272,56 @@ hgf_status hgf_serve_stats(hgf_server *s, hgf_serve_stats_t *out, int reset);
 hgf_status hgf_serve_inject_alloc_failures(hgf_server *s, int count);
 /* Drain the queue, wait for running requests, free everything. NULL is accepted. */
 hgf_status hgf_serve_destroy(hgf_server *s);
+
+/* ---------------------------------------------------------------------------------------------
+ * Cost volume of a stereo pair: the cost computation that precedes aggregation in the
+ * multi-label pipeline (Sec. 1; the cost-volume filtering framework of the stereo experiment,
+ * Sec. 6). The paper prints no formula; the library's reading is a truncated colour + gradient
+ * difference, for l = 0..L-1:
+ *   V(x, y, l) = alpha min(mean_c |I_c(x,y) - J_c(x',y)|, tau_color)
+ *              + (1 - alpha) min(|dI(x,y) - dJ(x',y)|, tau_grad),
+ *   x' = clamp(x - direction * l, 0, W - 1),
+ * I = ref, J = other, dI = 0.5 (g(x+1) - g(x-1)) of the channel mean g with neighbours clamped
+ * at the border. direction = +1 when ref is the left view, -1 when it is the right view.
+ * ref, other: device float32, C x H x W (C = 1 or 3). out: device, L x H x W of `dtype`
+ * (HGF_F32, HGF_BF16 or HGF_F16; computed in float32, rounded to nearest even). Enqueued on
+ * `stream`; HGF_EINVAL on NULL pointers, bad sizes, alpha outside [0, 1], negative thresholds,
+ * direction not +-1 or a bad dtype. */
+typedef struct {
+  double alpha;      /* colour weight (the gradient term gets 1 - alpha); 0.9 in the inputs here */
+  double tau_color;  /* truncation of the colour term (0.028) */
+  double tau_grad;   /* truncation of the gradient term (0.008) */
+  int direction;     /* +1: ref is the left view; -1: ref is the right view */
+} hgf_cost_params;
+hgf_status hgf_cost_volume(hgf_ctx *ctx, const float *ref, const float *other, int C, int H, int W,
+                           int L, const hgf_cost_params *p, int dtype, void *out, void *stream);
+
+/* Aggregation + WTA of the stereo cost volume of (guidance image, other), without storing the
+ * volume: the guidance handle's image is the reference view I, `other` (device float32,
+ * C x H x W, same shape as the guidance image) is J, and the coefficient kernel computes
+ * V(x, y, l) of hgf_cost_volume for labels l = 0..L-1 as it reads them (bit-identical to
+ * hgf_cost_volume with HGF_F32 storage followed by hgf_aggregate). Outputs as hgf_aggregate.
+ * Needs the fused path (2r+1 < 128; HGF_EUNSUPPORTED otherwise); errors as hgf_cost_volume and
+ * hgf_aggregate. */
+hgf_status hgf_aggregate_stereo(hgf_ctx *ctx, const hgf_guidance *g, const float *other, int L,
+                                const hgf_cost_params *p, void *filtered, int filtered_dtype,
+                                int32_t *labels, float *best, void *stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Post-WTA refinement of a stereo disparity map: the post-processing step that follows WTA in
+ * the cost-volume filtering framework of the stereo experiment (Sec. 6). The paper only names the
+ * step; the library's reading:
+ *  1. left-right consistency: left-view pixel (x, y) with d = disp_left(x, y) is kept when
+ *     d >= 0, x - d >= 0 and |d - disp_right(x - d, y)| <= threshold;
+ *  2. hole filling: every other pixel takes min(nearest kept disparity to its left, nearest kept
+ *     disparity to its right) on its row; with a kept pixel on one side only, that one; with none
+ *     on the row, its own disp_left.
+ * disp_left, disp_right: device int32 H x W (the labels of hgf_aggregate_stereo with direction
+ * +1 and -1, or of hgf_aggregate). out: device int32 H x W (must not alias the inputs). keep:
+ * device uint8 H x W scratch, receives 1 for kept pixels, 0 otherwise (caller-owned, required).
+ * Enqueued on `stream`; HGF_EINVAL on NULL pointers, H or W < 1, threshold < 0. */
+hgf_status hgf_refine_lr(hgf_ctx *ctx, const int32_t *disp_left, const int32_t *disp_right, int H,
+                         int W, int threshold, int32_t *out, uint8_t *keep, void *stream);
 
 /* ---------------------------------------------------------------------------------------------
  * Batched inverse of regularised Gram matrices: the paper's comparison of its recursion against a

@@ -16,6 +16,11 @@ code, tables or constants with the CUDA library; it restates the paper (arXiv 18
 * form B, the paper's own HGF (Sec. 4.1, Eq. HGF_linear_regression): G0 = 1, uncentred box sums,
   all n+1 coefficients penalised by lambda in sum units, Z by Eq. HGF_z2
 * WTA label selection (Sec. 1): argmin over labels, lowest label on ties, NaN treated as +inf
+* post-WTA refinement (Sec. 6 names the framework's post processing): left-right consistency
+  and hole filling, a reading (see refine_lr)
+* the cost volume V(x, y, l) of a stereo pair (Sec. 1; the cost computation step of the
+  cost-volume filtering framework of Sec. 6, whose formula the paper does not print: the reading
+  is a truncated colour + gradient difference, see cost_volume)
 
 Readings of the paper used here (where it is silent, ambiguous or garbled):
 * Prop. 1's base case is alpha^0_00 = -1/(lambda (lambda + G_00)); the printed -(lambda+G_00)^-1
@@ -268,6 +273,65 @@ def paper_filter(I, P, r, lam, degree, basis="powers", solver="hgf"):
     wa = box_sum(w, r) / N
     Z = np.einsum("kihw,ihw->khw", wa[:, 1:], Gn) + wa[:, 0]
     return Z[0] if single else Z
+
+
+# --------------------------------------------------------------------------------------------
+# Cost volume of a stereo pair (Sec. 1; reading of the framework's cost computation, Sec. 6)
+# --------------------------------------------------------------------------------------------
+def cost_volume(ref, other, L, alpha=0.9, tau_color=0.028, tau_grad=0.008, direction=1):
+    """V(x, y, l) = alpha min(mean_c |I_c(x,y) - J_c(x',y)|, tau_color)
+                  + (1 - alpha) min(|dI(x,y) - dJ(x',y)|, tau_grad),
+    x' = clamp(x - direction * l, 0, W-1), I = ref, J = other (C x H x W), dI the central
+    difference along x of the channel mean with clamped neighbours, 0.5 (g(x+1) - g(x-1)).
+    direction = 1: the reference is the left view (matches lie to the left in the right view);
+    -1: the reference is the right view. Returns float64 (L, H, W). One label at a time, plain
+    numpy."""
+    I = np.asarray(ref, dtype=np.float64)
+    J = np.asarray(other, dtype=np.float64)
+    C, H, W = I.shape
+    x = np.arange(W)
+    xp, xm = np.minimum(x + 1, W - 1), np.maximum(x - 1, 0)
+
+    def grad(img):
+        g = img.mean(axis=0)
+        return 0.5 * (g[:, xp] - g[:, xm])
+
+    dI, dJ = grad(I), grad(J)
+    V = np.empty((L, H, W))
+    for l in range(L):
+        xs = np.clip(x - direction * l, 0, W - 1)
+        col = np.abs(I - J[:, :, xs]).mean(axis=0)
+        grd = np.abs(dI - dJ[:, xs])
+        V[l] = alpha * np.minimum(col, tau_color) + (1.0 - alpha) * np.minimum(grd, tau_grad)
+    return V
+
+
+# --------------------------------------------------------------------------------------------
+# Post-WTA refinement (reading of the framework's post processing, Sec. 6)
+# --------------------------------------------------------------------------------------------
+def refine_lr(DL, DR, threshold=1):
+    """Left-right consistency check and hole filling, one pixel at a time.
+    keep(x, y): d = DL(x, y) >= 0, x - d >= 0 and |d - DR(x - d, y)| <= threshold.
+    Pixels not kept take min(nearest kept DL to the left, nearest kept DL to the right) on their
+    row; one side only: that one; none: their own DL. Returns (out, keep)."""
+    DL = np.asarray(DL)
+    DR = np.asarray(DR)
+    H, W = DL.shape
+    keep = np.zeros((H, W), dtype=bool)
+    for y in range(H):
+        for x in range(W):
+            d = int(DL[y, x])
+            keep[y, x] = d >= 0 and x - d >= 0 and abs(d - int(DR[y, x - d])) <= threshold
+    out = DL.copy()
+    for y in range(H):
+        for x in range(W):
+            if keep[y, x]:
+                continue
+            left = [int(DL[y, i]) for i in range(x - 1, -1, -1) if keep[y, i]][:1]
+            right = [int(DL[y, i]) for i in range(x + 1, W) if keep[y, i]][:1]
+            cand = left + right
+            out[y, x] = min(cand) if cand else DL[y, x]
+    return out, keep
 
 
 # --------------------------------------------------------------------------------------------

@@ -129,7 +129,7 @@ size_t aggregate_coef_bytes(const hgf_guidance *g, const AggregatePlan &p) {
 cudaError_t launch_aggregate(const hgf_guidance *g, const void *cost, int cost_dtype, int L,
                              float *filtered, int32_t *labels, float *best, float *coef_ws,
                              unsigned long long *keys, const AggregatePlan &p, cudaStream_t s,
-                             Profiler *prof) {
+                             Profiler *prof, const StereoSource *stereo) {
   const int HW = g->H * g->W;
   const bool want_wta = labels || best;
   unsigned long long *k = want_wta ? keys : nullptr;
@@ -137,13 +137,15 @@ cudaError_t launch_aggregate(const hgf_guidance *g, const void *cost, int cost_d
     cudaError_t e = cudaMemsetAsync(k, 0xff, (size_t)HW * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
   }
+  if (cost_dtype == kCostStereo && !stereo) return cudaErrorInvalidValue;
   const int b = basis_id(g->C, g->degree, g->basis);
   int *status = device_status_ptr();
   if (!status) return cudaErrorInvalidValue;
   cudaError_t e = cudaErrorInvalidValue;
   bool ok = dispatch_basis(b, [&](auto bc) {
     constexpr int B = decltype(bc)::value;
-    e = launch_basis<B>(g, cost, cost_dtype, L, filtered, coef_ws, k, p, status, s, prof);
+    e = launch_basis<B>(g, cost, cost_dtype, L, filtered, coef_ws, k, p, status,
+                        stereo ? *stereo : StereoSource{}, s, prof);
   });
   if (!ok) return cudaErrorInvalidValue;
   if (e != cudaSuccess) return e;

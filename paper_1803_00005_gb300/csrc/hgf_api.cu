@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <vector>
 #include <new>
 
 using namespace hgf;
@@ -275,7 +276,7 @@ hgf_status hgf_destroy(hgf_ctx *ctx) {
   }
   for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
   for (Workspace *w : {&ctx->ws_prepare, &ctx->ws_coef, &ctx->ws_keys, &ctx->ws_plain,
-                       &ctx->ws_io})
+                       &ctx->ws_io, &ctx->ws_grad})
     if (w->ptr) cudaFree(w->ptr);
   delete ctx;
   return HGF_OK;
@@ -370,6 +371,58 @@ hgf_status hgf_set_tuning(hgf_ctx *ctx, const hgf_tuning *t) {
     return set_err(ctx, HGF_EINVAL, "apply_mode must be 0, 1 or 2");
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   ctx->tuning = *t;
+  return HGF_OK;
+}
+
+hgf_status hgf_autotune(hgf_ctx *ctx, const hgf_guidance *g, const void *cost, int cost_dtype,
+                        int L, int32_t *labels, int reps, hgf_tuning *best, int *ncand,
+                        void *stream) {
+  hgf_status st = enter(ctx);
+  if (st != HGF_OK) return st;
+  st = check_outputs(ctx, g, cost, cost_dtype, L, nullptr, HGF_F32, labels, nullptr);
+  if (st != HGF_OK) return st;
+  if (!labels || reps < 1) return set_err(ctx, HGF_EINVAL, "labels is NULL or reps < 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  std::vector<hgf_tuning> cands;
+  for (int K : {2, 4, 8}) {
+    if (K != 2 && coef_smem(g->n, g->C, K, g->r) > 227 * 1024) continue;
+    for (int chunk : {0, 64, 16}) {
+      if (chunk != 0 && chunk >= L) continue;
+      for (int apply : {2, 1}) cands.push_back(hgf_tuning{K, 0, chunk, apply});
+    }
+  }
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  const hgf_tuning saved = ctx->tuning;
+  float best_ms = 0.f;
+  hgf_tuning pick = cands.front();
+  for (size_t i = 0; i < cands.size() && e == cudaSuccess && st == HGF_OK; ++i) {
+    ctx->tuning = cands[i];
+    st = aggregate_locked(ctx, g, cost, cost_dtype, L, nullptr, labels, nullptr, s);
+    if (st != HGF_OK) break;
+    e = cudaEventRecord(a, s);
+    for (int k = 0; k < reps && e == cudaSuccess && st == HGF_OK; ++k)
+      st = aggregate_locked(ctx, g, cost, cost_dtype, L, nullptr, labels, nullptr, s);
+    if (e == cudaSuccess) e = cudaEventRecord(b, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (e == cudaSuccess && (i == 0 || ms < best_ms)) {
+      best_ms = ms;
+      pick = cands[i];
+    }
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (st != HGF_OK || e != cudaSuccess) {
+    ctx->tuning = saved;
+    return st != HGF_OK ? st : cuda_fail_locked(ctx, e, "hgf_autotune");
+  }
+  ctx->tuning = pick;
+  if (best) *best = pick;
+  if (ncand) *ncand = (int)cands.size();
   return HGF_OK;
 }
 
@@ -476,6 +529,83 @@ hgf_status hgf_filter_host(hgf_ctx *ctx, const float *img, int C, int H, int W,
   e = read_device_status(&status, true);
   if (e != cudaSuccess) return cuda_fail_locked(ctx, e, "hgf_filter_host status");
   if (status != 0) return set_err(ctx, HGF_ETIMEOUT, "a bounded wait in a kernel ran out");
+  return HGF_OK;
+}
+
+hgf_status hgf_aggregate_stereo(hgf_ctx *ctx, const hgf_guidance *g, const float *other, int L,
+                                const hgf_cost_params *p, void *filtered, int filtered_dtype,
+                                int32_t *labels, float *best, void *stream) {
+  hgf_status st = enter(ctx);
+  if (st != HGF_OK) return st;
+  if (!other || !p) return set_err(ctx, HGF_EINVAL, "NULL argument");
+  // the cost is made here, not read: check the outputs with a stand-in cost pointer
+  st = check_outputs(ctx, g, other, HGF_F32, L, filtered, filtered_dtype, labels, best);
+  if (st != HGF_OK) return st;
+  if (!(p->alpha >= 0.0 && p->alpha <= 1.0) || !(p->tau_color >= 0.0) || !(p->tau_grad >= 0.0))
+    return set_err(ctx, HGF_EINVAL, "alpha must be in [0, 1] and thresholds >= 0");
+  if (p->direction != 1 && p->direction != -1)
+    return set_err(ctx, HGF_EINVAL, "direction must be +1 or -1");
+  if (!aggregate_fits(g))
+    return set_err(ctx, HGF_EUNSUPPORTED, "stereo aggregation needs 2r+1 < %d", kStripThreads);
+  cudaStream_t s = (cudaStream_t)stream;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  const size_t HW = (size_t)g->H * g->W;
+  AggregatePlan plan = plan_aggregate(g, L, ctx->tuning, ctx->num_sms);
+  st = grow(ctx, ctx->ws_coef, aggregate_coef_bytes(g, plan), s);
+  if (st == HGF_OK) st = grow(ctx, ctx->ws_keys, HW * sizeof(unsigned long long), s);
+  if (st == HGF_OK) st = grow(ctx, ctx->ws_grad, 2 * HW * sizeof(float), s);
+  if (st != HGF_OK) return st;
+  StereoSource src;
+  src.other = other;
+  src.grad = (const float *)ctx->ws_grad.ptr;
+  src.direction = p->direction;
+  src.alpha = (float)p->alpha;
+  src.tau_c = (float)p->tau_color;
+  src.tau_g = (float)p->tau_grad;
+  cudaError_t e = launch_grad_planes(g->img, other, g->C, g->H, g->W, (float *)ctx->ws_grad.ptr,
+                                     s, &ctx->prof);
+  if (e == cudaSuccess)
+    e = launch_aggregate(g, nullptr, kCostStereo, L, (float *)filtered, labels, best,
+                         (float *)ctx->ws_coef.ptr, (unsigned long long *)ctx->ws_keys.ptr, plan,
+                         s, &ctx->prof, &src);
+  if (e != cudaSuccess) return cuda_fail_locked(ctx, e, "hgf_aggregate_stereo");
+  return HGF_OK;
+}
+
+hgf_status hgf_refine_lr(hgf_ctx *ctx, const int32_t *disp_left, const int32_t *disp_right, int H,
+                         int W, int threshold, int32_t *out, uint8_t *keep, void *stream) {
+  hgf_status st = enter(ctx);
+  if (st != HGF_OK) return st;
+  if (!disp_left || !disp_right || !out || !keep) return set_err(ctx, HGF_EINVAL, "NULL argument");
+  if (H < 1 || W < 1 || (long long)H * W > (1ll << 31))
+    return set_err(ctx, HGF_EINVAL, "bad size %d x %d", H, W);
+  if (threshold < 0) return set_err(ctx, HGF_EINVAL, "threshold must be >= 0");
+  if (out == disp_left || out == disp_right) return set_err(ctx, HGF_EINVAL, "out aliases an input");
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  cudaError_t e = launch_refine_lr(disp_left, disp_right, H, W, threshold, out, keep,
+                                   (cudaStream_t)stream, &ctx->prof);
+  if (e != cudaSuccess) return cuda_fail_locked(ctx, e, "hgf_refine_lr");
+  return HGF_OK;
+}
+
+hgf_status hgf_cost_volume(hgf_ctx *ctx, const float *ref, const float *other, int C, int H, int W,
+                           int L, const hgf_cost_params *p, int dtype, void *out, void *stream) {
+  hgf_status st = enter(ctx);
+  if (st != HGF_OK) return st;
+  if (!ref || !other || !p || !out) return set_err(ctx, HGF_EINVAL, "NULL argument");
+  if ((C != 1 && C != 3) || H < 1 || W < 1 || L < 1)
+    return set_err(ctx, HGF_EINVAL, "bad sizes C=%d H=%d W=%d L=%d", C, H, W, L);
+  if ((long long)L * H * W > (1ll << 40)) return set_err(ctx, HGF_EINVAL, "volume too large");
+  if (!(p->alpha >= 0.0 && p->alpha <= 1.0) || !(p->tau_color >= 0.0) || !(p->tau_grad >= 0.0))
+    return set_err(ctx, HGF_EINVAL, "alpha must be in [0, 1] and thresholds >= 0");
+  if (p->direction != 1 && p->direction != -1)
+    return set_err(ctx, HGF_EINVAL, "direction must be +1 or -1");
+  if (dtype != HGF_F32 && dtype != HGF_BF16 && dtype != HGF_F16)
+    return set_err(ctx, HGF_EINVAL, "dtype must be HGF_F32, HGF_BF16 or HGF_F16");
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  cudaError_t e = launch_cost_volume(ref, other, C, H, W, L, *p, dtype, out,
+                                     (cudaStream_t)stream, &ctx->prof);
+  if (e != cudaSuccess) return cuda_fail_locked(ctx, e, "hgf_cost_volume");
   return HGF_OK;
 }
 

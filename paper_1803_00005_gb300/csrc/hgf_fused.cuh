@@ -20,12 +20,16 @@
 // means divide by the in-image count N(x, y).
 #pragma once
 #include "hgf_basis.cuh"
+#include "hgf_stereo.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace hgf {
 
 namespace {
+
+struct StereoTag {};  // cost type of k_coef when the cost is computed from a stereo pair
 
 constexpr int NT = kStripThreads;
 constexpr int kRowStride = NT + 4;  // [0..3] padding (index 3 holds the zero prefix), 4+t values
@@ -130,7 +134,8 @@ __global__ void __launch_bounds__(NT, (coef_min_blocks<B, K>())) k_coef(const CT
                                              const float *__restrict__ shift,
                                              const float *__restrict__ rec,
                                              float *__restrict__ coef, int l_first, int n_chunk,
-                                             int band_rows, int paper_form, int *status) {
+                                             int band_rows, int paper_form, int *status,
+                                             const StereoSource stereo) {
   constexpr int NG = basis_n(B), C1 = NG + 1, NC = basis_channels_in(B), RAW = NC + K;
   constexpr int REC = record_floats(NG), CP = coef_floats(NG);
   constexpr bool STAGE = stage_records<B>(), kCoefReload = coef_reload(NG);
@@ -181,15 +186,37 @@ __global__ void __launch_bounds__(NT, (coef_min_blocks<B, K>())) k_coef(const CT
     if (t == 0) issue_records(Y0);  // the first row has the warm-up rows to arrive
   }
 
-  const CT *cbase = cost + (size_t)(l_first + k0) * HW;
+  constexpr bool STEREO = std::is_same<CT, StereoTag>::value;
+  const CT *cbase = STEREO ? nullptr : cost + (size_t)(l_first + k0) * HW;
   auto load_row = [&](int row, float *v) {
     if (col_ok && row >= 0 && row < H) {
       const size_t pix = (size_t)row * W + xi;
 #pragma unroll
       for (int c = 0; c < NC; ++c) v[c] = __ldg(img + (size_t)c * HW + pix);
+      if constexpr (STEREO) {
+        // the cost of hgf_cost_volume, computed here: the guidance image is the reference view
+        const size_t rowoff = (size_t)row * W;
+        const float dI = __ldg(stereo.grad + pix);
 #pragma unroll
-      for (int k = 0; k < K; ++k)
-        v[NC + k] = k < nk ? load_cost(cbase, (size_t)k * HW + pix) : 0.f;
+        for (int k = 0; k < K; ++k) {
+          float val = 0.f;
+          if (k < nk) {
+            const int l = l_first + k0 + k;
+            const int xs = min(max(xi - stereo.direction * l, 0), W - 1);
+            float col = 0.f;
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+              col += fabsf(v[c] - __ldg(stereo.other + (size_t)c * HW + rowoff + xs));
+            val = stereo_cost(col, NC, dI, __ldg(stereo.grad + HW + rowoff + xs), stereo.alpha,
+                              stereo.tau_c, stereo.tau_g);
+          }
+          v[NC + k] = val;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+          v[NC + k] = k < nk ? load_cost(cbase, (size_t)k * HW + pix) : 0.f;
+      }
     }
   };
   float pa[RAW], pb[RAW], pc[RAW];
@@ -405,6 +432,8 @@ constexpr size_t apply_smem_bytes(int r) {
 
 // One label per CTA. RING: the outgoing coefficient row comes from the thread's shared-memory
 // ring; otherwise it is reloaded from device memory (used when the ring does not fit).
+// no minimum CTA count: capping registers for 5, 6 or 8 CTAs per SM made k_apply slower
+// (450x375, n = 9: 0.29 ms -> 0.41-0.44 ms)
 template <int B, bool RING>
 __global__ void __launch_bounds__(NT) k_apply(const float *__restrict__ coef, int H, int W, int r,
                                               const float *__restrict__ img,
@@ -580,8 +609,8 @@ static int resident_ctas(Kern k, size_t smem) {
 template <int B, int K>
 cudaError_t launch_chunk(const hgf_guidance *g, const void *cost, int cost_dtype, int l_first,
                          int nc, float *filtered, float *coef_ws, unsigned long long *keys,
-                         int band_rows, bool apply_ring, int *status, cudaStream_t s,
-                         Profiler *prof) {
+                         int band_rows, bool apply_ring, int *status,
+                         const StereoSource &stereo, cudaStream_t s, Profiler *prof) {
   const int H = g->H, W = g->W, r = g->r;
   const int TW = NT - 2 * r;
   const unsigned strips = (W + TW - 1) / TW;
@@ -593,6 +622,7 @@ cudaError_t launch_chunk(const hgf_guidance *g, const void *cost, int cost_dtype
     e = set_smem(k_coef<B, K, float>, sm);
     if (e == cudaSuccess) e = set_smem(k_coef<B, K, __nv_bfloat16>, sm);
     if (e == cudaSuccess) e = set_smem(k_coef<B, K, __half>, sm);
+    if (e == cudaSuccess) e = set_smem(k_coef<B, K, StereoTag>, sm);
     if (e != cudaSuccess) return e;
     const int passes = (nc + K - 1) / K;
     // bands planned for the two-label kernel whatever K is, so that K never changes a result
@@ -607,11 +637,12 @@ cudaError_t launch_chunk(const hgf_guidance *g, const void *cost, int cost_dtype
 #define HGF_COEF(CT)                                                                          \
   k_coef<B, K, CT><<<grid, NT, sm, s>>>((const CT *)cost, H, W, r, g->img, g->shift, g->rec,  \
                                         coef_ws, l_first, nc, rows,                           \
-                                        g->form == HGF_FORM_PAPER ? 1 : 0, status);
+                                        g->form == HGF_FORM_PAPER ? 1 : 0, status, stereo);
     switch (cost_dtype) {
       case HGF_F32: HGF_COEF(float) break;
       case HGF_BF16: HGF_COEF(__nv_bfloat16) break;
       case HGF_F16: HGF_COEF(__half) break;
+      case kCostStereo: HGF_COEF(StereoTag) break;
       default: return cudaErrorInvalidValue;
     }
 #undef HGF_COEF
@@ -650,19 +681,20 @@ cudaError_t launch_chunk(const hgf_guidance *g, const void *cost, int cost_dtype
 template <int B>
 cudaError_t launch_basis(const hgf_guidance *g, const void *cost, int cost_dtype, int L,
                          float *filtered, float *coef_ws, unsigned long long *keys,
-                         const AggregatePlan &p, int *status, cudaStream_t s, Profiler *prof) {
+                         const AggregatePlan &p, int *status, const StereoSource &stereo,
+                         cudaStream_t s, Profiler *prof) {
   cudaError_t e = cudaSuccess;
   for (int l0 = 0; l0 < L && e == cudaSuccess; l0 += p.chunk) {
     const int nc = std::min(p.chunk, L - l0);
     if (p.K == 4)
       e = launch_chunk<B, 4>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys, p.band_rows,
-                             p.apply_ring, status, s, prof);
+                             p.apply_ring, status, stereo, s, prof);
     else if (p.K == 8)
       e = launch_chunk<B, 8>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys, p.band_rows,
-                             p.apply_ring, status, s, prof);
+                             p.apply_ring, status, stereo, s, prof);
     else
       e = launch_chunk<B, 2>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys, p.band_rows,
-                             p.apply_ring, status, s, prof);
+                             p.apply_ring, status, stereo, s, prof);
   }
   return e;
 }
@@ -672,5 +704,6 @@ cudaError_t launch_basis(const hgf_guidance *g, const void *cost, int cost_dtype
 #define HGF_INSTANTIATE_BASIS(B)                                                               \
   template cudaError_t hgf::launch_basis<B>(const hgf_guidance *, const void *, int, int,      \
                                             float *, float *, unsigned long long *,           \
-                                            const hgf::AggregatePlan &, int *, cudaStream_t,  \
+                                            const hgf::AggregatePlan &, int *,                \
+                                            const hgf::StereoSource &, cudaStream_t,          \
                                             hgf::Profiler *);

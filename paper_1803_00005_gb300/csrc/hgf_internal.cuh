@@ -172,6 +172,7 @@ struct hgf_ctx {
   hgf::Workspace ws_keys;        // per-pixel WTA keys
   hgf::Workspace ws_plain;       // plain-form intermediates
   hgf::Workspace ws_io;          // device copies for hgf_filter_host
+  hgf::Workspace ws_grad;        // gradient planes of hgf_aggregate_stereo
   hgf_guidance *host_guidance = nullptr;  // reused by hgf_filter_host
   hgf_tuning tuning{0, 0, 0, 0};
   int num_sms = 0;
@@ -201,6 +202,16 @@ cudaError_t launch_prepare(hgf_guidance *g, const float *img, void *ws, size_t w
 size_t prepare_workspace_bytes(int n, int H, int W);
 cudaError_t launch_export(const hgf_guidance *g, float *minv_out, float *mu_out, cudaStream_t s);
 
+// Cost computed on the fly from a stereo pair (hgf_aggregate_stereo): the reference view is the
+// guidance image; `other` is the second view and grad holds both views' gradient planes
+// (reference first, H x W each). Passed by value to the coefficient kernel.
+struct StereoSource {
+  const float *other = nullptr;
+  const float *grad = nullptr;
+  int direction = 1;
+  float alpha = 0.f, tau_c = 0.f, tau_g = 0.f;
+};
+constexpr int kCostStereo = 100;  // cost_dtype of launch_aggregate for an on-the-fly stereo cost
 struct AggregatePlan {
   int K;            // labels per pass
   int band_rows;    // coefficient/output rows per CTA band (0: chosen per kernel from occupancy)
@@ -212,7 +223,7 @@ size_t aggregate_coef_bytes(const hgf_guidance *g, const AggregatePlan &p);
 cudaError_t launch_aggregate(const hgf_guidance *g, const void *cost, int cost_dtype, int L,
                              float *filtered, int32_t *labels, float *best, float *coef_ws,
                              unsigned long long *keys, const AggregatePlan &p, cudaStream_t s,
-                             Profiler *prof);
+                             Profiler *prof, const StereoSource *stereo = nullptr);
 size_t plain_workspace_bytes(const hgf_guidance *g, int L, int *chunk_out);
 cudaError_t launch_aggregate_plain(const hgf_guidance *g, const void *cost, int cost_dtype,
                                    int L, float *filtered, int32_t *labels, float *best,
@@ -225,6 +236,15 @@ hgf_status alloc_guidance_checked(hgf_ctx *ctx, int C, int H, int W, const hgf_p
                                   hgf_guidance **out);
 void free_guidance(hgf_guidance *g);
 bool aggregate_fits(const hgf_guidance *g);
+cudaError_t launch_grad_planes(const float *ref, const float *other, int C, int H, int W,
+                               float *out, cudaStream_t s, Profiler *prof);
+// Left-right consistency + hole filling (hgf_refine_lr).
+cudaError_t launch_refine_lr(const int32_t *dl, const int32_t *dr, int H, int W, int threshold,
+                             int32_t *out, uint8_t *keep, cudaStream_t s, Profiler *prof);
+// Stereo cost volume (hgf_cost_volume).
+cudaError_t launch_cost_volume(const float *ref, const float *other, int C, int H, int W, int L,
+                               const hgf_cost_params &p, int dtype, void *out, cudaStream_t s,
+                               Profiler *prof);
 // Batched (lambda E + S_i)^-1, packed, element-major over the batch (hgf_batched_inverse).
 cudaError_t launch_batched_inverse(const double *S, int count, int n, double lambda, int method,
                                    int precision, double *out, cudaStream_t s, Profiler *prof);
@@ -235,7 +255,8 @@ int *device_status_ptr();
 template <int B>
 cudaError_t launch_basis(const hgf_guidance *g, const void *cost, int cost_dtype, int L,
                          float *filtered, float *coef_ws, unsigned long long *keys,
-                         const AggregatePlan &p, int *status, cudaStream_t s, Profiler *prof);
+                         const AggregatePlan &p, int *status, const StereoSource &stereo,
+                         cudaStream_t s, Profiler *prof);
 // Reads (and, with clear, resets) the current device's watchdog word set by bounded waits.
 cudaError_t read_device_status(int *status, bool clear);  // fused kernels take this shape
 

@@ -36,7 +36,8 @@ EXPORTED = [
     "hgf_aggregate_static", "hgf_serve_create", "hgf_serve_submit", "hgf_serve_poll",
     "hgf_serve_wait", "hgf_serve_stats", "hgf_serve_inject_alloc_failures", "hgf_serve_destroy",
     "hgf_batch_create", "hgf_batch_run", "hgf_batch_launch_graph", "hgf_batch_destroy",
-    "hgf_device_status", "hgf_batched_inverse",
+    "hgf_device_status", "hgf_batched_inverse", "hgf_cost_volume", "hgf_aggregate_stereo",
+    "hgf_refine_lr", "hgf_autotune",
 ]
 
 
@@ -51,6 +52,11 @@ class hgf_params(ctypes.Structure):
     _fields_ = [("degree", ctypes.c_int), ("basis", ctypes.c_int), ("r", ctypes.c_int),
                 ("eps", ctypes.c_double), ("inv_precision", ctypes.c_int),
                 ("combine", ctypes.c_int), ("form", ctypes.c_int)]
+
+
+class hgf_cost_params(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("tau_color", ctypes.c_double),
+                ("tau_grad", ctypes.c_double), ("direction", ctypes.c_int)]
 
 
 class hgf_tuning(ctypes.Structure):
@@ -132,6 +138,13 @@ def lib():
         "hgf_launch_count": (c_int, [vp, P(ctypes.c_ulonglong)]),
         "hgf_device_status": (c_int, [vp, P(c_int), c_int]),
         "hgf_batched_inverse": (c_int, [vp, vp, c_int, c_int, c_double, c_int, c_int, vp, vp]),
+        "hgf_cost_volume": (c_int, [vp, vp, vp, c_int, c_int, c_int, c_int, P(hgf_cost_params),
+                                    c_int, vp, vp]),
+        "hgf_aggregate_stereo": (c_int, [vp, vp, vp, c_int, P(hgf_cost_params), vp, c_int, vp,
+                                         vp, vp]),
+        "hgf_refine_lr": (c_int, [vp, vp, vp, c_int, c_int, c_int, vp, vp, vp]),
+        "hgf_autotune": (c_int, [vp, vp, vp, c_int, c_int, vp, c_int, P(hgf_tuning), P(c_int),
+                                 vp]),
         "hgf_profile_enable": (c_int, [vp, c_int]),
         "hgf_profile_report": (c_int, [vp, ctypes.c_char_p, ctypes.c_size_t]),
     }
@@ -332,6 +345,74 @@ def hgf_batched_inverse(ctx, S, n, lam, method="prop1", precision="f64", out=Non
         HGF_INV_PROP1 if method == "prop1" else HGF_INV_CHOLESKY, DTYPE_CODES[precision],
         _ptr(out), _stream(stream)))
     return out
+
+
+def hgf_cost_volume(ctx, ref, other, L, out=None, dtype="f32", alpha=0.9, tau_color=0.028,
+                    tau_grad=0.008, direction=1, stream=None):
+    """Stereo cost volume V (L, H, W) of the float32 (C, H, W) views `ref` and `other` on the
+    device; returns `out` (allocated when None; a bfloat16/float16/float32 tensor)."""
+    _require_cuda(ref, "ref")
+    _require_cuda(other, "other")
+    C, H, W = ref.shape
+    if tuple(other.shape) != (C, H, W):
+        raise ValueError("ref and other must have the same shape")
+    if out is None:
+        import torch
+        tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[dtype]
+        out = torch.empty((L, H, W), dtype=tdt, device=ref.device)
+    _require_cuda(out, "out")
+    p = hgf_cost_params(alpha=float(alpha), tau_color=float(tau_color), tau_grad=float(tau_grad),
+                        direction=int(direction))
+    _check(ctx, lib().hgf_cost_volume(ctx, _ptr(ref), _ptr(other), C, H, W, int(L),
+                                      ctypes.byref(p), _dtype_code(out), _ptr(out),
+                                      _stream(stream)))
+    return out
+
+
+def hgf_aggregate_stereo(ctx, g, other, L, filtered=None, labels=None, best=None, alpha=0.9,
+                         tau_color=0.028, tau_grad=0.008, direction=1, stream=None):
+    """Aggregation + WTA of the stereo cost of (guidance image, other) computed on the fly."""
+    for t, nm in ((other, "other"), (filtered, "filtered"), (labels, "labels"), (best, "best")):
+        _require_cuda(t, nm)
+    p = hgf_cost_params(alpha=float(alpha), tau_color=float(tau_color), tau_grad=float(tau_grad),
+                        direction=int(direction))
+    _check(ctx, lib().hgf_aggregate_stereo(ctx, g, _ptr(other), int(L), ctypes.byref(p),
+                                           _ptr(filtered), HGF_F32, _ptr(labels), _ptr(best),
+                                           _stream(stream)))
+
+
+def hgf_refine_lr(ctx, disp_left, disp_right, threshold=1, out=None, keep=None, stream=None):
+    """Left-right consistency + hole filling of int32 (H, W) disparity maps on the device;
+    returns (out, keep)."""
+    import torch
+    for t, nm in ((disp_left, "disp_left"), (disp_right, "disp_right")):
+        _require_cuda(t, nm)
+        if t.dtype != torch.int32:
+            raise ValueError(f"{nm} must be int32")
+    H, W = disp_left.shape
+    if out is None:
+        out = torch.empty_like(disp_left)
+    if keep is None:
+        keep = torch.empty((H, W), dtype=torch.uint8, device=disp_left.device)
+    _require_cuda(out, "out")
+    _require_cuda(keep, "keep")
+    _check(ctx, lib().hgf_refine_lr(ctx, _ptr(disp_left), _ptr(disp_right), H, W, int(threshold),
+                                    _ptr(out), _ptr(keep), _stream(stream)))
+    return out, keep
+
+
+def hgf_autotune(ctx, g, cost, labels, reps=3, stream=None):
+    """Times every result-preserving tuning on (g, cost), keeps the fastest on ctx; returns
+    (tuning dict, candidates timed)."""
+    _require_cuda(cost, "cost")
+    _require_cuda(labels, "labels")
+    t = hgf_tuning()
+    n = ctypes.c_int()
+    _check(ctx, lib().hgf_autotune(ctx, g, _ptr(cost), _dtype_code(cost), cost.shape[0],
+                                   _ptr(labels), int(reps), ctypes.byref(t), ctypes.byref(n),
+                                   _stream(stream)))
+    return dict(labels_per_pass=t.labels_per_pass, band_rows=t.band_rows,
+                chunk_labels=t.chunk_labels, apply_mode=t.apply_mode), n.value
 
 
 def hgf_device_status(ctx, clear=False):

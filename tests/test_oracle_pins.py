@@ -359,3 +359,85 @@ def test_filter_at_matches_full_image():
     got = O.filter_at(I, P, r, 1e-4, 2, pts)
     for t, (y, x) in enumerate(pts):
         np.testing.assert_allclose(got[:, t], q[:, y, x], rtol=1e-12, atol=1e-15)
+
+
+# ------------------------------------------------------------------------------- cost volume
+def test_cost_volume_zero_at_the_true_shift():
+    """A scene point at left x seen at right x - d (right(x') = left(x' + d)): the
+    left-reference cost is exactly 0 at label d wherever x - d and the gradient neighbours are
+    inside both views (d + 1 <= x <= W - 2) and positive at the other labels there; identical
+    views cost 0 at label 0; the right-reference cost (direction -1) of the same pair is 0 at
+    label d for 1 <= x <= W - d - 2."""
+    rng = np.random.Generator(np.random.PCG64(3))
+    H, W, d = 5, 23, 4
+    base = rng.uniform(0, 1, (3, H, W + d))
+    left, right = base[:, :, :W], base[:, :, d:d + W]
+    V = O.cost_volume(left, right, 8)
+    assert np.all(V[d][:, d + 1:W - 1] == 0.0)
+    others = np.delete(V[:, :, d + 1:W - 1], d, axis=0)
+    assert np.all(others > 0.0)
+    assert np.all(O.cost_volume(left, left, 1) == 0.0)
+    VR = O.cost_volume(right, left, 8, direction=-1)
+    assert np.all(VR[d][:, 1:W - d - 1] == 0.0)
+
+
+def test_cost_volume_constant_offset_closed_form():
+    """Constant views with per-channel offsets delta_c: gradients vanish, so
+    V = alpha min(mean_c |delta_c|, tau_color) for every label and pixel (truncation and the
+    alpha weight are pinned by choosing offsets on both sides of tau_color)."""
+    for delta, alpha in (((0.01, -0.02, 0.005), 0.9), ((0.1, 0.2, -0.3), 0.6)):
+        I = np.full((3, 4, 9), 0.5)
+        J = I + np.array(delta)[:, None, None]
+        V = O.cost_volume(I, J, 5, alpha=alpha, tau_color=0.028, tau_grad=0.008)
+        want = alpha * min(np.mean(np.abs(delta)), 0.028)
+        np.testing.assert_allclose(V, want, rtol=1e-15, atol=0)
+
+
+def test_cost_volume_ramp_gradient_and_border_clamp():
+    """Identical horizontal ramps I_c = J_c = a x: the colour term is alpha min(a l, tau_color)
+    wherever x - l >= 0, the gradient term vanishes in the interior (both slopes a) and at the
+    clamped border the match column is x' = 0, so V(x, l) for x < l equals the cost at
+    x' = 0: alpha min(a x, tau_color) + (1 - alpha) min(|dI(x) - dJ(0)|, tau_grad) with
+    dJ(0) = a / 2 (one-sided neighbour) and dI(x) = a inside."""
+    a, W, L, alpha = 0.004, 16, 6, 0.9
+    I = np.tile(a * np.arange(W, dtype=np.float64), (3, 2, 1))
+    V = O.cost_volume(I, I, L, alpha=alpha, tau_color=0.015, tau_grad=0.008)
+    for l in range(L):
+        for x in range(W):
+            xs = max(x - l, 0)
+            col = alpha * min(a * (x - xs), 0.015)
+            dI = a if 0 < x < W - 1 else a / 2
+            dJ = a if 0 < xs < W - 1 else a / 2
+            want = col + (1 - alpha) * min(abs(dI - dJ), 0.008)
+            assert abs(V[l, 0, x] - want) < 1e-15, (l, x)
+
+
+# ------------------------------------------------------------------------- post-WTA refinement
+def test_refine_lr_hand_worked_rows():
+    """Hand-worked rows (threshold 1). Row 0: DL = DR warped consistently except an occlusion
+    band at x = 3, 4 (disparities 5 pointing outside, 0 inconsistent): filled with the smaller
+    neighbour 1. Row 1: nothing consistent: DL unchanged. Row 2: kept pixels on the right only:
+    the nearest one to the right fills."""
+    DL = np.array([[0, 1, 1, 5, 0, 2, 2, 2],
+                   [7, 7, 7, 7, 7, 7, 7, 7],
+                   [9, 9, 9, 0, 0, 1, 1, 1]])
+    DR = np.array([[0, 1, 1, 1, 2, 2, 2, 2],
+                   [0, 0, 0, 0, 0, 0, 0, 0],
+                   [0, 0, 0, 0, 1, 1, 1, 1]])
+    out, keep = O.refine_lr(DL, DR, 1)
+    # row 0: x=3: d=5 -> x-d<0 drop; x=4: d=0 -> DR(4)=2, |0-2|>1 drop; others consistent
+    assert keep[0].tolist() == [True, True, True, False, False, True, True, True]
+    assert out[0].tolist() == [0, 1, 1, 1, 1, 2, 2, 2]
+    assert not keep[1].any() and out[1].tolist() == DL[1].tolist()
+    # row 2: x<3: d=9 outside; x=3,4: d=0 -> DR=0 at 3 (kept), DR(4)=1 (|0-1|<=1 kept)
+    assert keep[2].tolist() == [False, False, False, True, True, True, True, True]
+    assert out[2].tolist() == [0, 0, 0, 0, 0, 1, 1, 1]
+
+
+def test_refine_lr_consistent_maps_unchanged():
+    """Maps from a fronto-parallel plane at disparity d (DL = DR = d) are consistent wherever
+    x >= d; the left border x < d is filled from the first kept pixel (d)."""
+    DL = np.full((3, 10), 3)
+    out, keep = O.refine_lr(DL, DL, 0)
+    assert keep[:, 3:].all() and not keep[:, :3].any()
+    assert (out == 3).all()
