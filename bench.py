@@ -110,7 +110,77 @@ def parse():
     ap.add_argument("--inverse", action="store_true",
                     help="batched-inverse microbenchmark: Prop. 1 vs per-matrix Cholesky")
     ap.add_argument("--count", type=int, default=1_000_000, help="inverse: matrices per batch")
+    ap.add_argument("--table3", action="store_true",
+                    help="the paper's Table 3 shape: one gray slice, paper form, n = 3..9 powers")
     return ap.parse_args()
+
+
+# Table 3 of the paper (GTX 960, ArrayFire; ms per filtered slice), context only
+PAPER_TABLE3_MS = {250: (3.9, 10.7, 39.9, 110.2), 500: (3.7, 11.1, 40.1, 112.4),
+                   1000: (4.1, 10.9, 41.3, 115.9), 2000: (4.3, 11.2, 42.7, 121.8)}
+
+
+def table3_arm(args):
+    """The paper's Table 3 workload shape: a gray image of 250^2 .. 2000^2 filtering one slice
+    (itself) with the paper's own form (G_0 = 1, uncentred sums, lambda = 0.05 in sum units,
+    r = 7) and power guidance I, I^2, .., I^n for n = 3, 5, 7, 9. One step = guidance precompute
+    + aggregation of the slice with the filtered output written. Median of `steps` CUDA-event
+    timed steps after warm-up, L2 flushed between steps."""
+    import numpy as np
+    import torch
+    from paper_1803_00005_gb300 import build, hgf, synth
+    build.build()
+    torch.cuda.set_device(0)
+    ctx = hgf.hgf_create(0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    reps = max(5, min(args.steps, 50))
+    table = []
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = hgf.hgf_launch_count(ctx)
+    for size in (250, 500, 1000, 2000):
+        left, _, _ = synth.stereo_pair(size, size, 16, 300 + size)
+        gray = left.mean(axis=0, keepdims=True).astype(np.float32)
+        img = torch.from_numpy(gray).cuda()
+        cost = img.clone()                                  # the slice: the image itself
+        out = torch.empty_like(cost)
+        for j, n in enumerate((3, 5, 7, 9)):
+            g = hgf.hgf_prepare(ctx, img, hgf.make_params(degree=n, r=7, eps=0.05,
+                                                          basis="powers", form="paper"))
+            for _ in range(max(3, args.warmup)):
+                hgf.hgf_guidance_update(ctx, g, img)
+                hgf.hgf_aggregate(ctx, g, cost, filtered=out)
+            ms = []
+            for i in range(reps):
+                flush.fill_(i & 0xff)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                hgf.hgf_guidance_update(ctx, g, img)
+                hgf.hgf_aggregate(ctx, g, cost, filtered=out)
+                b.record(stream)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+            hgf.hgf_guidance_release(g)
+            t = statistics.median(ms)
+            table.append(dict(size=size, n=n, ms=t, mpx_per_s=size * size / t / 1e3,
+                              paper_gtx960_ms=PAPER_TABLE3_MS[size][j]))
+    clk = clocks.stop()
+    launches = hgf.hgf_launch_count(ctx) - launches0
+    hgf.hgf_destroy(ctx)
+    key = next(r for r in table if r["size"] == 1000 and r["n"] == 9)
+    line = dict(metric="ms per filtered gray slice, paper form, n=9 powers, 1000x1000",
+                value=key["ms"], unit="ms", n_gpus=1, steps=reps, warmup=max(3, args.warmup),
+                ms_per_step=key["ms"], higher_is_better=False, scaling="weak", vs_baseline=None,
+                dtype="f32 (f64 inverse)", data="synthetic", impl="table3",
+                config=dict(workload="gray 250^2..2000^2, one slice, paper form, lambda=0.05, "
+                                     "r=7, powers n=3,5,7,9 (the shape of the paper's Table 3)",
+                            l2="256 MiB flush between steps",
+                            step="guidance precompute + aggregate (filtered output)"),
+                table=table, gpu_launches=launches, clocks=clk,
+                note="paper_gtx960_ms: the paper's Table 3 (GTX 960), context only")
+    print(json.dumps(line), flush=True)
 
 
 def inverse_arm(args):
@@ -313,6 +383,59 @@ print(json.dumps(dict(times=times, units=cw * ch * P.shape[0])))
 """
 
 
+ORACLE_POOL_SNIPPET = r"""
+import json, os, sys, time, multiprocessing as mp
+sys.path.insert(0, {root!r})
+
+def work(args):
+    import numpy as np
+    from oracle import hgf_oracle as O
+    I, P, w = args
+    q = O.centred_filter(I, P, w["r"], w["eps"], w["degree"])
+    return np.argmin(q, axis=0)
+
+if __name__ == "__main__":
+    import numpy as np
+    from paper_1803_00005_gb300 import synth
+    w = {w!r}
+    case = synth.make_case(w["width"], w["height"], w["n_labels"], w["seed"], w["dtype"])
+    cw, ch = {crop!r}
+    H, W = w["height"], w["width"]
+    y0, x0 = (H - ch) // 2, (W - cw) // 2
+    I = case.guidance[:, y0:y0 + ch, x0:x0 + cw]
+    P = synth.from_dtype(case.cost[:, y0:y0 + ch, x0:x0 + cw], w["dtype"])
+    cores = len(os.sched_getaffinity(0))
+    chunks = [c for c in np.array_split(np.arange(P.shape[0]), cores) if len(c)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(len(chunks)) as pool:
+        pool.map(work, [(I[:, :4, :4], P[c][:, :4, :4], w) for c in chunks])   # start-up
+        times = []
+        for rep in range({reps}):
+            t = time.perf_counter()
+            pool.map(work, [(I, P[c], w) for c in chunks])
+            times.append(time.perf_counter() - t)
+    print(json.dumps(dict(times=times, units=cw * ch * P.shape[0], cores=len(chunks))))
+"""
+
+
+def run_oracle_pool(w, crop, reps):
+    """Times the CPU oracle with the labels split over every host core (one spawned process per
+    core, each with one BLAS/OpenMP thread; each process recomputes the guidance part)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ORACLE_POOL_SNIPPET.format(root=ROOT, w=w, crop=tuple(crop), reps=reps)
+    with tempfile.NamedTemporaryFile("w", suffix=".py", delete=False) as f:
+        f.write(code)
+        path = f.name
+    try:
+        out = subprocess.run([sys.executable, path], capture_output=True, text=True, env=env,
+                             timeout=1800)
+    finally:
+        os.unlink(path)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
 def run_oracle(w, crop, reps):
     """Times the CPU oracle (float64, single thread) on a centred crop with all labels, in a
     fresh interpreter (no GPU state, BLAS/OpenMP pinned to one thread)."""
@@ -404,6 +527,8 @@ def main():
         return batch_arm(args)
     if args.inverse:
         return inverse_arm(args)
+    if args.table3:
+        return table3_arm(args)
     if args.impl == "reference":
         return reference_arm(args, w)
 
@@ -411,7 +536,7 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
 
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu:
         crop = (min(args.cpu_crop[0], w["width"]), min(args.cpu_crop[1], w["height"]))
         res = run_oracle(w, crop, 2)            # before any GPU work in this process
@@ -421,6 +546,15 @@ def main():
                    sample=f"centred {crop[0]}x{crop[1]} crop, all {w['n_labels']} labels, "
                           f"prepare + aggregate + WTA, 2 repetitions ({tot:.1f} s), float64 numpy, "
                           f"one thread")
+        try:
+            resp = run_oracle_pool(w, crop, 2)
+            tp = sum(resp["times"])
+            cpu_all = dict(value=resp["units"] * len(resp["times"]) / tp / 1e6, unit=UNIT,
+                           cores=resp["cores"], kind="oracle",
+                           sample=f"same crop, labels split over {resp['cores']} spawned "
+                                  f"processes (one thread each), 2 repetitions ({tp:.1f} s)")
+        except (RuntimeError, subprocess.TimeoutExpired, OSError) as exc:
+            cpu_all = dict(value=None, error=str(exc)[-300:])
 
     import numpy as np
     import torch
@@ -510,6 +644,21 @@ def main():
                         peak_note=("nominal float64 rate" if dom == "k_inverse" else
                                    "152 SMs x 128 FP32 lanes x 2 x 2070 MHz"))
 
+    # whole-step HBM fraction from the algorithmic bytes per px*label: the cost read once plus
+    # the guidance image, inverse record and label write per pixel (amortised over L)
+    sc = {"f32": 4, "bf16": 2, "f16": 2}[w["dtype"]]
+    bytes_per_unit = sc + (12 + 4 * (n * (n + 1) // 2 + n) + 4) / L
+    hbm_peak = None
+    try:
+        hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except (OSError, ValueError, KeyError):
+        pass
+    hbm = None
+    if hbm_peak:
+        gbs = bytes_per_unit * H * W * L * args.steps / t_max / 1e9 * world
+        hbm = dict(algorithmic_gbs=gbs, peak_gbs=hbm_peak, frac=gbs / hbm_peak,
+                   bytes_per_px_label=bytes_per_unit, peak_note="measured (MEASURED_PEAKS.json)")
+
     e2e = None
     if not args.no_e2e:
         pin_img = torch.from_numpy(case.guidance).pin_memory()
@@ -576,7 +725,8 @@ def main():
                     config=dict(workload=w["name"], parallelism=f"replicas x{world}",
                                 l2="256 MiB buffer written between timed steps",
                                 step="guidance precompute + aggregate + WTA"),
-                    roofline=roof, cpu_baseline=cpu, e2e=e2e, e2e_stereo=e2e_stereo,
+                    roofline=roof, hbm=hbm, cpu_baseline=cpu,
+                    cpu_baseline_all_cores=cpu_all, e2e=e2e, e2e_stereo=e2e_stereo,
                     gpu_launches=int(launches),
                     clocks=clk, kernels=kernels, wall_s=wall,
                     step_ms=dict(min=min(step_ms), median=statistics.median(step_ms)))

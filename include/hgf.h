@@ -74,6 +74,9 @@ typedef struct {
   int inv_precision;  /* HGF_F64 (default) or HGF_F32: precision of Sigma assembly + recursion */
   int combine;        /* hgf_combine */
   int form;           /* hgf_form (0 = CENTRED) */
+  int compensated;    /* 1: Kahan-compensated vertical running sums in the guidance-moment and
+                       * aggregation kernels (two labels per pass; slower, smaller rounding
+                       * error); 0: plain float32 running sums (default) */
 } hgf_params;
 
 typedef struct hgf_ctx hgf_ctx;

@@ -49,7 +49,9 @@ __global__ void k_wta_volume(const float *__restrict__ q, int L, int HW,
 size_t coef_smem(int n, int C, int K, int r) {
   const bool stage = records_strip_tiled(n);
   return 16 + sizeof(float) * ((size_t)2 * K * (n + 1) * kRowStride +
-                               (stage ? (size_t)2 * record_floats(n) * (NT - 2 * r) : 0) +
+                               (stage ? (size_t)kRecordBuffers * record_floats(n) *
+                                            (NT - 2 * r)
+                                      : 0) +
                                (coef_reload(n) ? 0 : (size_t)(2 * r + 1) * (C + K) * NT));
 }
 
@@ -99,6 +101,7 @@ AggregatePlan plan_aggregate(const hgf_guidance *g, int L, const hgf_tuning &t, 
   // 1400x1100 13.3 / 16.4 / 26.9 ms). K never changes a result (each label's arithmetic is the
   // same for any K).
   p.K = 2;
+  p.nominal = std::max(2, std::min(64, (L + 1) / 2 * 2));
   if (t.labels_per_pass == 2 ||
       ((t.labels_per_pass == 4 || t.labels_per_pass == 8) &&
        coef_smem(g->n, g->C, t.labels_per_pass, g->r) <= 227 * 1024))

@@ -105,6 +105,8 @@ hgf_status check_params(hgf_ctx *ctx, int C, int H, int W, const hgf_params *p, 
     return set_err(ctx, HGF_EINVAL, "unknown combine %d", p->combine);
   if (p->form != HGF_FORM_CENTRED && p->form != HGF_FORM_PAPER)
     return set_err(ctx, HGF_EINVAL, "unknown form %d", p->form);
+  if (p->compensated != 0 && p->compensated != 1)
+    return set_err(ctx, HGF_EINVAL, "compensated must be 0 or 1");
   int n = hgf_num_channels(C, p->degree, p->basis);
   if (n < 1) return set_err(ctx, HGF_EUNSUPPORTED, "C=%d degree=%d basis=%d gives n > %d", C,
                             p->degree, p->basis, kMaxChannels);
@@ -133,6 +135,7 @@ hgf_status alloc_guidance(hgf_ctx *ctx, int C, int H, int W, int n, const hgf_pa
   g->inv_precision = p->inv_precision;
   g->combine = p->combine;
   g->form = p->form;
+  g->compensated = p->compensated;
   const size_t HW = (size_t)H * W;
   const size_t rec_floats = record_total_floats(H, W, n, g->r);
   const size_t floats = HW * ((size_t)C + n + packed_size(n) + n) + rec_floats + 64;
@@ -157,7 +160,8 @@ hgf_status alloc_guidance(hgf_ctx *ctx, int C, int H, int W, int n, const hgf_pa
 bool same_shape(const hgf_guidance *g, int C, int H, int W, const hgf_params *p) {
   return g && g->C == C && g->H == H && g->W == W && g->degree == p->degree &&
          g->basis == p->basis && g->r == effective_radius(p->r, H, W) && g->eps == p->eps &&
-         g->inv_precision == p->inv_precision && g->combine == p->combine && g->form == p->form;
+         g->inv_precision == p->inv_precision && g->combine == p->combine && g->form == p->form &&
+         g->compensated == p->compensated;
 }
 
 hgf_status prepare_locked(hgf_ctx *ctx, hgf_guidance *g, const float *img, cudaStream_t s) {

@@ -21,6 +21,7 @@
 #pragma once
 #include "hgf_basis.cuh"
 #include "hgf_stereo.cuh"
+#include "hgf_scan.cuh"
 
 #include <algorithm>
 #include <type_traits>
@@ -31,53 +32,10 @@ namespace {
 
 struct StereoTag {};  // cost type of k_coef when the cost is computed from a stereo pair
 
-constexpr int NT = kStripThreads;
-constexpr int kRowStride = NT + 4;  // [0..3] padding (index 3 holds the zero prefix), 4+t values
-
-// Inclusive prefix sums along each shared row (values at [4 .. 4+NT)), one warp per row.
-// All rows of a warp are loaded first and their shuffle chains advance together, so the chain
-// latency is paid once per warp rather than once per row. Warp w scans rows w, w+4, w+8, ..
-// (RPW of them at most) among the first `rows`.
-template <int RPW>
-__device__ __forceinline__ void scan_rows(float *sA, int rows) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int NW = NT / 32;
-  float4 v[RPW];
-  float tot[RPW];
-#pragma unroll
-  for (int j = 0; j < RPW; ++j) {
-    const int row = warp + j * NW;
-    v[j] = row < rows ? *(reinterpret_cast<float4 *>(sA + row * kRowStride + 4) + lane)
-                      : make_float4(0.f, 0.f, 0.f, 0.f);
-    v[j].y += v[j].x;
-    v[j].z += v[j].y;
-    v[j].w += v[j].z;
-    tot[j] = v[j].w;
-  }
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-#pragma unroll
-    for (int j = 0; j < RPW; ++j) {
-      const float o = __shfl_up_sync(0xffffffffu, tot[j], off);
-      if (lane >= off) tot[j] += o;
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < RPW; ++j) {
-    const int row = warp + j * NW;
-    const float ex = tot[j] - v[j].w;
-    v[j].x += ex;
-    v[j].y += ex;
-    v[j].z += ex;
-    v[j].w += ex;
-    if (row < rows) *(reinterpret_cast<float4 *>(sA + row * kRowStride + 4) + lane) = v[j];
-  }
-}
-
-// Window sum [t, t + 2r] of a scanned shared row.
-__device__ __forceinline__ float window(const float *row, int t, int r) {
-  return row[4 + t + 2 * r] - row[3 + t];
-}
+using strip::NT;
+using strip::kRowStride;
+using strip::scan_rows;
+using strip::window;
 
 // ---- bulk asynchronous copies of inverse records into shared memory (mbarrier completion)
 constexpr int kWaitLimit = 1 << 22;  // try_wait polls before a wait gives up (seconds, not cycles)
@@ -121,15 +79,28 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
 template <int B>
 __host__ __device__ constexpr bool stage_records() { return records_strip_tiled(basis_n(B)); }
 
+
 // CTAs per SM that shared memory leaves room for when the records are staged (r = 9: three at two
 // labels per pass, two at four), passed to __launch_bounds__ as the register budget
-template <int B, int K>
+template <int B, int K, bool COMP>
 __host__ __device__ constexpr int coef_min_blocks() {
-  return !stage_records<B>() ? 1 : K <= 2 ? 3 : K <= 4 ? 2 : 1;
+  return !stage_records<B>() ? 1
+         : (K <= 2 && !COMP) ? (kRecordBuffers == 1 ? 4 : 3)
+         : K <= 4 ? 2 : 1;
 }
 
-template <int B, int K, typename CT>
-__global__ void __launch_bounds__(NT, (coef_min_blocks<B, K>())) k_coef(const CT *__restrict__ cost, int H, int W, int r,
+// Compensated (Kahan) update s += x: c carries the low-order part lost so far, and the sum is
+// s - c. Used by the kernels' COMP instantiations for the vertical running sums, where each row
+// adds one sample and removes another, so rounding errors would otherwise accumulate over a band.
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+template <int B, int K, typename CT, bool COMP>
+__global__ void __launch_bounds__(NT, (coef_min_blocks<B, K, COMP>())) k_coef(const CT *__restrict__ cost, int H, int W, int r,
                                              const float *__restrict__ img,
                                              const float *__restrict__ shift,
                                              const float *__restrict__ rec,
@@ -147,7 +118,7 @@ __global__ void __launch_bounds__(NT, (coef_min_blocks<B, K>())) k_coef(const CT
   float *sA0 = smem + 4;
   const int TW = NT - 2 * r;
   float *recs = sA0 + 2 * K * C1 * kRowStride;      // [2][REC][TW] record rows (STAGE)
-  float *ring = recs + (STAGE ? 2 * REC * TW : 0);  // [2r+1][RAW][NT], thread-private
+  float *ring = recs + (STAGE ? kRecordBuffers * REC * TW : 0);  // [2r+1][RAW][NT], private
   __shared__ int s_fail;
   const int R = 2 * r + 1;
   const size_t HW = (size_t)H * W;
@@ -172,8 +143,13 @@ __global__ void __launch_bounds__(NT, (coef_min_blocks<B, K>())) k_coef(const CT
   const size_t strips = gridDim.y;
   auto rec_block = [&](int y) { return rec + ((size_t)y * strips + blockIdx.y) * REC * TW; };
   const uint32_t rec_bytes = (uint32_t)(REC * TW * sizeof(float));
+  // buffer and mbarrier of row y, and the phase parity its copy completes
+  auto rbuf = [&](int y) { return kRecordBuffers == 1 ? 0 : (y - Y0) & 1; };
+  auto rpar = [&](int y) -> uint32_t {
+    return kRecordBuffers == 1 ? (y - Y0) & 1 : ((y - Y0) >> 1) & 1;
+  };
   auto issue_records = [&](int y) {  // thread 0 only
-    bulk_copy_g2s(recs + ((y - Y0) & 1) * REC * TW, rec_block(y), rec_bytes, &bars[(y - Y0) & 1]);
+    bulk_copy_g2s(recs + rbuf(y) * REC * TW, rec_block(y), rec_bytes, &bars[rbuf(y)]);
   };
   if (STAGE) {
     if (t == 0) {
@@ -235,10 +211,15 @@ __global__ void __launch_bounds__(NT, (coef_min_blocks<B, K>())) k_coef(const CT
   load_old(s_begin + 1 - 2 * r - 1, ob);
 
   float V[K][C1];
+  float Vc[COMP ? K : 1][COMP ? C1 : 1];  // Kahan compensation terms (COMP only)
 #pragma unroll
   for (int k = 0; k < K; ++k)
 #pragma unroll
     for (int c = 0; c < C1; ++c) V[k][c] = 0.f;
+#pragma unroll
+  for (int k = 0; k < (COMP ? K : 1); ++k)
+#pragma unroll
+    for (int c = 0; c < (COMP ? C1 : 1); ++c) Vc[k][c] = 0.f;
 
   // One step per input row s: `cur` holds row s (loaded two steps earlier) and row s + 2 is
   // loaded into `nxt`. The loop is unrolled three times so that the three buffers rotate roles
@@ -263,9 +244,15 @@ __global__ void __launch_bounds__(NT, (coef_min_blocks<B, K>())) k_coef(const CT
 #pragma unroll
         for (int k = 0; k < K; ++k) {
           const float p = kCoefReload ? cur_o[kCoefReload ? NC + k : 0] : slot[(NC + k) * NT];
-          V[k][0] -= p;
+          if constexpr (COMP) {
+            kahan_add(V[k][0], Vc[k][0], -p);
 #pragma unroll
-          for (int i = 0; i < NG; ++i) V[k][i + 1] = fmaf(-go[i], p, V[k][i + 1]);
+            for (int i = 0; i < NG; ++i) kahan_add(V[k][i + 1], Vc[k][i + 1], -go[i] * p);
+          } else {
+            V[k][0] -= p;
+#pragma unroll
+            for (int i = 0; i < NG; ++i) V[k][i + 1] = fmaf(-go[i], p, V[k][i + 1]);
+          }
         }
       }
       if (s >= 0 && s < H) {
@@ -278,9 +265,15 @@ __global__ void __launch_bounds__(NT, (coef_min_blocks<B, K>())) k_coef(const CT
 #pragma unroll
         for (int k = 0; k < K; ++k) {
           const float p = cur[NC + k];
-          V[k][0] += p;
+          if constexpr (COMP) {
+            kahan_add(V[k][0], Vc[k][0], p);
 #pragma unroll
-          for (int i = 0; i < NG; ++i) V[k][i + 1] = fmaf(g[i], p, V[k][i + 1]);
+            for (int i = 0; i < NG; ++i) kahan_add(V[k][i + 1], Vc[k][i + 1], g[i] * p);
+          } else {
+            V[k][0] += p;
+#pragma unroll
+            for (int i = 0; i < NG; ++i) V[k][i + 1] = fmaf(g[i], p, V[k][i + 1]);
+          }
         }
       }
     }
@@ -291,17 +284,22 @@ __global__ void __launch_bounds__(NT, (coef_min_blocks<B, K>())) k_coef(const CT
 #pragma unroll
     for (int k = 0; k < K; ++k)
 #pragma unroll
-      for (int c = 0; c < C1; ++c) sA[(k * C1 + c) * kRowStride + 4 + t] = V[k][c];
+      for (int c = 0; c < C1; ++c)
+        sA[(k * C1 + c) * kRowStride + 4 + t] = COMP ? V[k][c] - Vc[COMP ? k : 0][COMP ? c : 0]
+                                                     : V[k][c];
     __syncthreads();
-    // every thread is past the previous row's phase C: the other record buffer is free
-    if (STAGE && t == 0 && y1 + 1 < Y1) issue_records(y1 + 1);
+    // every thread is past the previous row's phase C: that row's record buffer is free
+    if (STAGE && t == 0) {
+      if (kRecordBuffers == 2 && y1 + 1 < Y1) issue_records(y1 + 1);
+      if (kRecordBuffers == 1 && y1 > Y0) issue_records(y1);
+    }
     scan_rows<(K * C1 + NT / 32 - 1) / (NT / 32)>(sA, nk * C1);
-    if (STAGE && !mbar_wait(&bars[(y1 - Y0) & 1], ((y1 - Y0) >> 1) & 1)) s_fail = 1;
+    if (STAGE && !mbar_wait(&bars[rbuf(y1)], rpar(y1))) s_fail = 1;
     __syncthreads();
     if (STAGE && s_fail) {  // a copy never completed: report, drain with a bound, stop
       if (t == 0) {
         atomicExch(status, 1);
-        if (y1 + 1 < Y1) mbar_wait(&bars[(y1 + 1 - Y0) & 1], ((y1 + 1 - Y0) >> 1) & 1);
+        if (kRecordBuffers == 2 && y1 + 1 < Y1) mbar_wait(&bars[rbuf(y1 + 1)], rpar(y1 + 1));
       }
       failed = true;
       return;
@@ -311,7 +309,7 @@ __global__ void __launch_bounds__(NT, (coef_min_blocks<B, K>())) k_coef(const CT
     if (coef_here) {
       const size_t pix = (size_t)y1 * W + x;
       const float invN = 1.f / (float)(clipped_count(x, r, W) * clipped_count(y1, r, H));
-      const float *rrow = recs + ((y1 - Y0) & 1) * REC * TW + t;
+      const float *rrow = recs + rbuf(y1) * REC * TW + t;
       int stride = TW;  // made opaque per label pair below so that addresses are not hoisted
       auto recv = [&](int e) -> float {
         return STAGE ? rrow[e * stride] : __ldg(rec + pix * REC + e);
@@ -434,7 +432,7 @@ constexpr size_t apply_smem_bytes(int r) {
 // ring; otherwise it is reloaded from device memory (used when the ring does not fit).
 // no minimum CTA count: capping registers for 5, 6 or 8 CTAs per SM made k_apply slower
 // (450x375, n = 9: 0.29 ms -> 0.41-0.44 ms)
-template <int B, bool RING>
+template <int B, bool RING, bool COMP>
 __global__ void __launch_bounds__(NT) k_apply(const float *__restrict__ coef, int H, int W, int r,
                                               const float *__restrict__ img,
                                               const float *__restrict__ shift,
@@ -489,9 +487,15 @@ __global__ void __launch_bounds__(NT) k_apply(const float *__restrict__ coef, in
   load_row(s_begin + 1, pb);
   load_old(s_begin - 2 * r - 1, oa);
   load_old(s_begin + 1 - 2 * r - 1, ob);
-  float V[C1];
+  float V[C1], Vc[COMP ? C1 : 1];
 #pragma unroll
   for (int c = 0; c < C1; ++c) V[c] = 0.f;
+#pragma unroll
+  for (int c = 0; c < (COMP ? C1 : 1); ++c) Vc[c] = 0.f;
+  auto acc = [&](int c, float x) {  // V[c] += x, compensated in the COMP instantiation
+    if constexpr (COMP) kahan_add(V[c], Vc[c], x);
+    else V[c] += x;
+  };
 
   // Same three-buffer rotation as k_coef; without the ring, the outgoing row (2r+1 rows back,
   // resident in L2) is prefetched two steps ahead as well.
@@ -514,23 +518,23 @@ __global__ void __launch_bounds__(NT) k_apply(const float *__restrict__ coef, in
         float *slot = ring + (size_t)(((s - s_begin) % R) * C1) * NT + t;
         if (so >= add_lo) {
 #pragma unroll
-          for (int c = 0; c < C1; ++c) V[c] -= slot[c * NT];
+          for (int c = 0; c < C1; ++c) acc(c, -slot[c * NT]);
         }
         if (s >= 0 && s < H) {
 #pragma unroll
           for (int c = 0; c < C1; ++c) {
-            V[c] += cur[c];
+            acc(c, cur[c]);
             slot[c * NT] = cur[c];
           }
         }
       } else {
         if (so >= add_lo) {
 #pragma unroll
-          for (int c = 0; c < C1; ++c) V[c] -= cur_o[c];
+          for (int c = 0; c < C1; ++c) acc(c, -cur_o[c]);
         }
         if (s >= 0 && s < H) {
 #pragma unroll
-          for (int c = 0; c < C1; ++c) V[c] += cur[c];
+          for (int c = 0; c < C1; ++c) acc(c, cur[c]);
         }
       }
     }
@@ -538,7 +542,8 @@ __global__ void __launch_bounds__(NT) k_apply(const float *__restrict__ coef, in
     float *sA = sA0 + ((y2 - Y0) & 1) * C1 * kRowStride;
 
 #pragma unroll
-    for (int c = 0; c < C1; ++c) sA[c * kRowStride + 4 + t] = V[c];
+    for (int c = 0; c < C1; ++c)
+      sA[c * kRowStride + 4 + t] = COMP ? V[c] - Vc[COMP ? c : 0] : V[c];
     __syncthreads();
     scan_rows<(C1 + NT / 32 - 1) / (NT / 32)>(sA, C1);
     __syncthreads();
@@ -573,9 +578,10 @@ cudaError_t set_smem(Kern k, size_t bytes) {
 
 // Rows per band for a kernel whose grid is strips x bands x slabs: the band count that minimises
 // (waves of resident CTAs) x (rows streamed per CTA, including the 2r warm-up rows). Callers pass
-// a nominal slab count that depends on the shape only (not on how many labels a call or chunk
-// has): the band boundaries decide the order of the running sums, so results are then identical
-// whether an image is aggregated alone, in a batch, in the serving loop or in label chunks.
+// a nominal slab count fixed per call (from min(64, L), never from the chunk or from K): the band
+// boundaries decide the order of the running sums, so results are then identical whether an
+// image is aggregated alone, in a batch, in the serving loop, in label chunks or with any K.
+// Small label counts get more, shorter bands, so that a single slice still fills the GPU.
 static int choose_band_rows(int H, int r, long long strips_slabs, int resident) {
   long long best_cost = -1;
   int best = H;
@@ -592,8 +598,6 @@ static int choose_band_rows(int H, int r, long long strips_slabs, int resident) 
   return best;
 }
 
-constexpr int kNominalLabels = 64;  // label count the band heights are planned for
-
 template <typename Kern>
 static int resident_ctas(Kern k, size_t smem) {
   int dev = 0, sms = 0, per_sm = 0;
@@ -606,10 +610,10 @@ static int resident_ctas(Kern k, size_t smem) {
   return std::max(1, per_sm) * std::max(1, sms);
 }
 
-template <int B, int K>
+template <int B, int K, bool COMP>
 cudaError_t launch_chunk(const hgf_guidance *g, const void *cost, int cost_dtype, int l_first,
                          int nc, float *filtered, float *coef_ws, unsigned long long *keys,
-                         int band_rows, bool apply_ring, int *status,
+                         int band_rows, bool apply_ring, int nominal, int *status,
                          const StereoSource &stereo, cudaStream_t s, Profiler *prof) {
   const int H = g->H, W = g->W, r = g->r;
   const int TW = NT - 2 * r;
@@ -619,25 +623,27 @@ cudaError_t launch_chunk(const hgf_guidance *g, const void *cost, int cost_dtype
     const size_t sm = coef_smem(basis_n(B), basis_channels_in(B), K, r);
     // the shared-memory limit is raised before the occupancy query so that every call (the
     // first included) plans the same bands
-    e = set_smem(k_coef<B, K, float>, sm);
-    if (e == cudaSuccess) e = set_smem(k_coef<B, K, __nv_bfloat16>, sm);
-    if (e == cudaSuccess) e = set_smem(k_coef<B, K, __half>, sm);
-    if (e == cudaSuccess) e = set_smem(k_coef<B, K, StereoTag>, sm);
+    e = set_smem(k_coef<B, K, float, COMP>, sm);
+    if (e == cudaSuccess) e = set_smem(k_coef<B, K, __nv_bfloat16, COMP>, sm);
+    if (e == cudaSuccess) e = set_smem(k_coef<B, K, __half, COMP>, sm);
+    if (e == cudaSuccess) e = set_smem(k_coef<B, K, StereoTag, COMP>, sm);
     if (e != cudaSuccess) return e;
     const int passes = (nc + K - 1) / K;
-    // bands planned for the two-label kernel whatever K is, so that K never changes a result
+    // bands planned for the two-label, uncompensated kernel whatever K is, so that K never
+    // changes a result and compensation changes only the rounding of the sums
     const size_t sm2 = coef_smem(basis_n(B), basis_channels_in(B), 2, r);
-    e = set_smem(k_coef<B, 2, float>, sm2);
+    e = set_smem(k_coef<B, 2, float, false>, sm2);
     if (e != cudaSuccess) return e;
     const int rows = band_rows > 0 ? band_rows
-                                   : choose_band_rows(H, r, (long long)strips * (kNominalLabels / 2),
-                                                      resident_ctas(k_coef<B, 2, float>, sm2));
+                                   : choose_band_rows(H, r, (long long)strips * std::max(1, nominal / 2),
+                                                      resident_ctas(k_coef<B, 2, float, false>, sm2));
     dim3 grid(passes, strips, (H + rows - 1) / rows);
     LaunchScope ls(prof, "k_coef", s);
 #define HGF_COEF(CT)                                                                          \
-  k_coef<B, K, CT><<<grid, NT, sm, s>>>((const CT *)cost, H, W, r, g->img, g->shift, g->rec,  \
-                                        coef_ws, l_first, nc, rows,                           \
-                                        g->form == HGF_FORM_PAPER ? 1 : 0, status, stereo);
+  k_coef<B, K, CT, COMP><<<grid, NT, sm, s>>>((const CT *)cost, H, W, r, g->img, g->shift,    \
+                                              g->rec, coef_ws, l_first, nc, rows,             \
+                                              g->form == HGF_FORM_PAPER ? 1 : 0, status,      \
+                                              stereo);
     switch (cost_dtype) {
       case HGF_F32: HGF_COEF(float) break;
       case HGF_BF16: HGF_COEF(__nv_bfloat16) break;
@@ -650,25 +656,33 @@ cudaError_t launch_chunk(const hgf_guidance *g, const void *cost, int cost_dtype
   {
     LaunchScope ls(prof, "k_apply", s);
     const size_t ring_sm = apply_smem_bytes<B, true>(r);
-    if (apply_ring && ring_sm <= 227 * 1024) {
-      e = set_smem(k_apply<B, true>, ring_sm);
-      if (e != cudaSuccess) return e;
-      const int rows = band_rows > 0 ? band_rows
-                                     : choose_band_rows(H, r, (long long)strips * kNominalLabels,
-                                                        resident_ctas(k_apply<B, true>, ring_sm));
-      dim3 grid(nc, strips, (H + rows - 1) / rows);
-      k_apply<B, true><<<grid, NT, ring_sm, s>>>(coef_ws, H, W, r, g->img, g->shift, keys,
-                                                 filtered, l_first, rows);
-    } else {
+    bool ringed = false;
+    if constexpr (!COMP) {
+      if (apply_ring && ring_sm <= 227 * 1024) {
+        ringed = true;
+        e = set_smem(k_apply<B, true, false>, ring_sm);
+        if (e != cudaSuccess) return e;
+        const int rows = band_rows > 0 ? band_rows
+                                       : choose_band_rows(H, r, (long long)strips * nominal,
+                                                          resident_ctas(k_apply<B, true, false>,
+                                                                        ring_sm));
+        dim3 grid(nc, strips, (H + rows - 1) / rows);
+        k_apply<B, true, false><<<grid, NT, ring_sm, s>>>(coef_ws, H, W, r, g->img, g->shift,
+                                                          keys, filtered, l_first, rows);
+      }
+    }
+    if (!ringed) {
       const size_t sm = apply_smem_bytes<B, false>(r);
-      e = set_smem(k_apply<B, false>, sm);
+      e = set_smem(k_apply<B, false, COMP>, sm);
+      if (e == cudaSuccess && COMP) e = set_smem(k_apply<B, false, false>, sm);
       if (e != cudaSuccess) return e;
       const int rows = band_rows > 0 ? band_rows
-                                     : choose_band_rows(H, r, (long long)strips * kNominalLabels,
-                                                        resident_ctas(k_apply<B, false>, sm));
+                                     : choose_band_rows(H, r, (long long)strips * nominal,
+                                                        resident_ctas(k_apply<B, false, false>,
+                                                                      sm));
       dim3 grid(nc, strips, (H + rows - 1) / rows);
-      k_apply<B, false><<<grid, NT, sm, s>>>(coef_ws, H, W, r, g->img, g->shift, keys, filtered,
-                                             l_first, rows);
+      k_apply<B, false, COMP><<<grid, NT, sm, s>>>(coef_ws, H, W, r, g->img, g->shift, keys,
+                                                   filtered, l_first, rows);
     }
   }
   return cudaGetLastError();
@@ -686,15 +700,18 @@ cudaError_t launch_basis(const hgf_guidance *g, const void *cost, int cost_dtype
   cudaError_t e = cudaSuccess;
   for (int l0 = 0; l0 < L && e == cudaSuccess; l0 += p.chunk) {
     const int nc = std::min(p.chunk, L - l0);
-    if (p.K == 4)
-      e = launch_chunk<B, 4>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys, p.band_rows,
-                             p.apply_ring, status, stereo, s, prof);
+    if (g->compensated)  // compensated sums: two labels per pass only
+      e = launch_chunk<B, 2, true>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys,
+                                   p.band_rows, false, p.nominal, status, stereo, s, prof);
+    else if (p.K == 4)
+      e = launch_chunk<B, 4, false>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys, p.band_rows,
+                             p.apply_ring, p.nominal, status, stereo, s, prof);
     else if (p.K == 8)
-      e = launch_chunk<B, 8>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys, p.band_rows,
-                             p.apply_ring, status, stereo, s, prof);
+      e = launch_chunk<B, 8, false>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys, p.band_rows,
+                             p.apply_ring, p.nominal, status, stereo, s, prof);
     else
-      e = launch_chunk<B, 2>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys, p.band_rows,
-                             p.apply_ring, status, stereo, s, prof);
+      e = launch_chunk<B, 2, false>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys, p.band_rows,
+                             p.apply_ring, p.nominal, status, stereo, s, prof);
   }
   return e;
 }

@@ -53,6 +53,16 @@ inline size_t record_total_floats(int H, int W, int n, int r) {
   return (size_t)H * ((W + tw - 1) / tw) * tw * record_floats(n);
 }
 
+#ifndef HGF_RECORD_BUFFERS
+#define HGF_RECORD_BUFFERS 1
+#endif
+// Record blocks staged per CTA: 2 = the next row's block arrives while the current row is
+// processed; 1 (default) = the next row's copy starts once every thread is done with the current
+// row's records and is hidden by that row's vertical update and scans. One buffer halves the
+// shared memory of the records, so four CTAs fit on an SM instead of three: k_coef 0.39 -> 0.33 ms
+// (450x375, L = 60) and 13.8 -> 11.0 ms (1400x1100, L = 256), n = 9, r = 9.
+constexpr int kRecordBuffers = HGF_RECORD_BUFFERS;
+
 #ifndef HGF_COEF_RELOAD
 #define HGF_COEF_RELOAD -1
 #endif
@@ -184,6 +194,7 @@ struct hgf_guidance {
   int C = 0, H = 0, W = 0, n = 0, degree = 0, basis = 0, r = 0;
   double eps = 0.0;
   int inv_precision = HGF_F64, combine = HGF_COMBINE_ALPHA, form = HGF_FORM_CENTRED;
+  int compensated = 0;     // Kahan-compensated running sums in the strip kernels
   float *img = nullptr;    // C x H x W, copy of the input image
   float *G = nullptr;      // n x H x W, shifted guidance G_i - c_i
   float *minv = nullptr;   // n(n+1)/2 x H x W, packed (Sigma + eps E)^-1 (centred form only)
@@ -217,6 +228,8 @@ struct AggregatePlan {
   int band_rows;    // coefficient/output rows per CTA band (0: chosen per kernel from occupancy)
   int chunk;        // labels per workspace chunk
   bool apply_ring;  // output kernel keeps the outgoing rows in a shared-memory ring
+  int nominal;      // label count the band heights are planned for: min(64, L rounded up to
+                    // even), the same for every chunk of a call so chunking never changes a result
 };
 AggregatePlan plan_aggregate(const hgf_guidance *g, int L, const hgf_tuning &t, int num_sms);
 size_t aggregate_coef_bytes(const hgf_guidance *g, const AggregatePlan &p);

@@ -9,6 +9,7 @@
 // precision chosen by hgf_params.inv_precision (float64 by default).
 #include "hgf_basis.cuh"
 #include "hgf_prop1.cuh"
+#include "hgf_scan.cuh"
 
 #include <algorithm>
 
@@ -139,7 +140,165 @@ __global__ void k_shifted_guidance(const float *__restrict__ img, const float *_
   for (int i = 0; i < N; ++i) G[(size_t)i * HW + p] = g[i];
 }
 
+// ------------------------------------------------------------------ moment window sums (strips)
+// The window sums of every moment channel in one pass, for n <= 9: a CTA walks down a band of
+// rows over a 128-column strip (one thread per column, 2r halo columns), keeps the vertical
+// window sums of the M = n + n(n+1)/2 channels in registers (adding the entering row's
+// products, subtracting those of the row leaving the window, re-read from L2), and forms the
+// horizontal window sums by prefix scans of shared rows. Channel m < n is G_m; m >= n is the
+// pair (i, j), i <= j, of the packed upper triangle.
+template <int NG, bool COMP>
+__global__ void __launch_bounds__(kStripThreads) k_moments(const float *__restrict__ G, int H,
+                                                           int W, int r, int band_rows,
+                                                           float *__restrict__ mom) {
+  using namespace strip;
+  constexpr int M = NG + NG * (NG + 1) / 2;
+  constexpr int RPW = (M + NT / 32 - 1) / (NT / 32);
+  extern __shared__ __align__(16) float smem[];  // two scan buffers of M rows, alternate rows
+  const size_t HW = (size_t)H * W;
+  const int t = threadIdx.x;
+  const int TW = NT - 2 * r;
+  const int x0 = blockIdx.x * TW;
+  const int xc = x0 - r + t;
+  const bool col_ok = xc >= 0 && xc < W;
+  const int Y0 = blockIdx.y * band_rows;
+  const int Y1 = min(H, Y0 + band_rows);
+  const int add_lo = max(0, Y0 - r);
+  const int s_begin = Y0 - r, s_end = Y1 + r;
+  for (int i = t; i < 2 * M; i += NT) smem[i * kRowStride + 3] = 0.f;
+
+  auto ld_new = [&](int row, float *v) {
+    if (col_ok && row >= 0 && row < H) {
+#pragma unroll
+      for (int i = 0; i < NG; ++i) v[i] = __ldg(G + (size_t)i * HW + (size_t)row * W + xc);
+    }
+  };
+  auto ld_old = [&](int row, float *v) {  // rows that entered this band's windows only
+    if (col_ok && row >= add_lo && row < H) {
+#pragma unroll
+      for (int i = 0; i < NG; ++i) v[i] = __ldg(G + (size_t)i * HW + (size_t)row * W + xc);
+    }
+  };
+  float pa[NG], pb[NG], pc[NG], oa[NG], ob[NG], oc[NG];
+#pragma unroll
+  for (int i = 0; i < NG; ++i) pa[i] = pb[i] = pc[i] = oa[i] = ob[i] = oc[i] = 0.f;
+  ld_new(s_begin, pa);
+  ld_new(s_begin + 1, pb);
+  ld_old(s_begin - 2 * r - 1, oa);
+  ld_old(s_begin - 2 * r, ob);
+  float V[M], Vc[COMP ? M : 1];  // running sums and (COMP) their Kahan compensation terms
+#pragma unroll
+  for (int m = 0; m < M; ++m) V[m] = 0.f;
+#pragma unroll
+  for (int m = 0; m < (COMP ? M : 1); ++m) Vc[m] = 0.f;
+  auto acc = [&](int m, float x) {
+    if constexpr (COMP) {
+      const float y = x - Vc[m];
+      const float t2 = V[m] + y;
+      Vc[m] = (t2 - V[m]) - y;
+      V[m] = t2;
+    } else {
+      V[m] += x;
+    }
+  };
+
+  // three-buffer rotation: row s + 2 (and the row leaving two steps later) load while row s works
+  auto step = [&](const int s, const float *cur, float *nxt, const float *cur_o, float *nxt_o) {
+    if (s >= s_end) return;
+    ld_new(s + 2, nxt);
+    ld_old(s + 1 - 2 * r, nxt_o);
+    if (col_ok) {
+      if (s - 2 * r - 1 >= add_lo) {
+#pragma unroll
+        for (int i = 0; i < NG; ++i) {
+          acc(i, -cur_o[i]);
+#pragma unroll
+          for (int j = i; j < NG; ++j) {
+            if constexpr (COMP)
+              acc(NG + tri_index(NG, i, j), -cur_o[i] * cur_o[j]);
+            else
+              V[NG + tri_index(NG, i, j)] = fmaf(-cur_o[i], cur_o[j], V[NG + tri_index(NG, i, j)]);
+          }
+        }
+      }
+      if (s >= 0 && s < H) {
+#pragma unroll
+        for (int i = 0; i < NG; ++i) {
+          acc(i, cur[i]);
+#pragma unroll
+          for (int j = i; j < NG; ++j) {
+            if constexpr (COMP)
+              acc(NG + tri_index(NG, i, j), cur[i] * cur[j]);
+            else
+              V[NG + tri_index(NG, i, j)] = fmaf(cur[i], cur[j], V[NG + tri_index(NG, i, j)]);
+          }
+        }
+      }
+    }
+    const int y2 = s - r;
+    if (y2 < Y0) return;  // warm-up rows (uniform per CTA)
+    float *sA = smem + ((y2 - Y0) & 1) * M * kRowStride;
+#pragma unroll
+    for (int m = 0; m < M; ++m) sA[m * kRowStride + 4 + t] = COMP ? V[m] - Vc[COMP ? m : 0] : V[m];
+    __syncthreads();
+    scan_rows<RPW>(sA, M);
+    __syncthreads();
+    const int x = x0 + t;
+    if (t < TW && x < W) {
+      const size_t pix = (size_t)y2 * W + x;
+#pragma unroll
+      for (int m = 0; m < M; ++m) mom[(size_t)m * HW + pix] = window(sA + m * kRowStride, t, r);
+    }
+  };
+  for (int s = s_begin; s < s_end; s += 3) {
+    step(s, pa, pc, oa, oc);
+    step(s + 1, pb, pa, ob, oa);
+    step(s + 2, pc, pb, oc, ob);
+  }
+}
+
+template <int NG, bool COMP>
+cudaError_t launch_moments_strip(const float *G, int H, int W, int r, int num_sms, float *mom,
+                                 cudaStream_t s, Profiler *prof) {
+  constexpr int M = NG + NG * (NG + 1) / 2;
+  const size_t sm = sizeof(float) * 2 * M * strip::kRowStride;
+  cudaError_t e = cudaSuccess;
+  if (sm > 48 * 1024) {
+    e = cudaFuncSetAttribute(k_moments<NG, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sm);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_moments<NG, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)sm);
+  }
+  if (e != cudaSuccess) return e;
+  // bands planned from the uncompensated kernel's occupancy: compensation changes rounding only
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_moments<NG, false>, kStripThreads,
+                                                    sm) != cudaSuccess)
+    per_sm = 1;
+  const long long resident = (long long)std::max(1, per_sm) * std::max(1, num_sms);
+  const int TW = kStripThreads - 2 * r;
+  const int strips = (W + TW - 1) / TW;
+  // band count minimising (waves of resident CTAs) x (rows streamed, with the 2r warm-up rows)
+  long long best_cost = -1;
+  int rows = H;
+  for (int bands = 1; bands <= std::max(1, H / std::max(8, 2 * r)); ++bands) {
+    const int rw = (H + bands - 1) / bands;
+    const long long ctas = (long long)strips * ((H + rw - 1) / rw);
+    const long long cost = ((ctas + resident - 1) / resident) * (rw + 2 * r);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      rows = rw;
+    }
+  }
+  dim3 grid(strips, (H + rows - 1) / rows);
+  LaunchScope ls(prof, "k_moments", s);
+  k_moments<NG, COMP><<<grid, kStripThreads, sm, s>>>(G, H, W, r, rows, mom);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------------- moment row sums
+// Direct sums for n = 19 (too many channels for registers) and windows wider than a strip.
 // Moment channel m < n is G_m; m >= n enumerates the pairs (i, j), i <= j, of the packed upper
 // triangle. rows[m][y][x] = sum over the clipped horizontal window of the channel's values.
 __global__ void k_moment_rows(const float *__restrict__ G, int n, int H, int W, int r,
@@ -414,15 +573,35 @@ cudaError_t launch_prepare(hgf_guidance *g, const float *img, void *ws, size_t w
       k_shifted_guidance<B><<<(HW + 255) / 256, 256, 0, s>>>(g->img, g->shift, HW, g->G);
     }
   });
-  {
-    dim3 grid((W + 127) / 128, H, (unsigned)M);
-    LaunchScope ls(prof, "k_moment_rows", s);
-    k_moment_rows<<<grid, 128, 0, s>>>(g->G, n, H, W, g->r, rows);
-  }
-  {
-    dim3 grid((W + 127) / 128, H, (unsigned)M);
-    LaunchScope ls(prof, "k_moment_cols", s);
-    k_moment_cols<<<grid, 128, 0, s>>>(rows, H, W, g->r, mom);
+  if (n <= 9 && 2 * g->r + 1 < kStripThreads) {
+    int dev = 0, sms = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 1;
+    switch (n) {
+#define HGF_MOM_CASE(N) \
+  case N:               \
+    e = g->compensated ? launch_moments_strip<N, true>(g->G, H, W, g->r, sms, mom, s, prof)   \
+                       : launch_moments_strip<N, false>(g->G, H, W, g->r, sms, mom, s, prof); \
+    break;
+      HGF_MOM_CASE(1) HGF_MOM_CASE(2) HGF_MOM_CASE(3) HGF_MOM_CASE(4) HGF_MOM_CASE(5)
+      HGF_MOM_CASE(6) HGF_MOM_CASE(7) HGF_MOM_CASE(8) HGF_MOM_CASE(9)
+#undef HGF_MOM_CASE
+      default:
+        e = cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+  } else {
+    {
+      dim3 grid((W + 127) / 128, H, (unsigned)M);
+      LaunchScope ls(prof, "k_moment_rows", s);
+      k_moment_rows<<<grid, 128, 0, s>>>(g->G, n, H, W, g->r, rows);
+    }
+    {
+      dim3 grid((W + 127) / 128, H, (unsigned)M);
+      LaunchScope ls(prof, "k_moment_cols", s);
+      k_moment_cols<<<grid, 128, 0, s>>>(rows, H, W, g->r, mom);
+    }
   }
   bool ok = g->inv_precision == HGF_F32 ? launch_inverse_n<float>(mom, g, s, prof)
                                         : launch_inverse_n<double>(mom, g, s, prof);

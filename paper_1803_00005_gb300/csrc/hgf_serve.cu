@@ -35,12 +35,12 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
 
 struct CacheKey {
   uint64_t key;
-  int C, H, W, degree, basis, r, prec, combine, form;
+  int C, H, W, degree, basis, r, prec, combine, form, comp;
   double eps;
   bool operator<(const CacheKey &o) const {
-    return std::tie(key, C, H, W, degree, basis, r, prec, combine, form, eps) <
+    return std::tie(key, C, H, W, degree, basis, r, prec, combine, form, comp, eps) <
            std::tie(o.key, o.C, o.H, o.W, o.degree, o.basis, o.r, o.prec, o.combine, o.form,
-                    o.eps);
+                    o.comp, o.eps);
   }
 };
 
@@ -147,7 +147,8 @@ struct hgf_server {
     Slot &sl = slots[si];
     const hgf_request &r = q->r;
     CacheKey key{r.guidance_key, r.C, r.H, r.W, r.params.degree, r.params.basis, r.params.r,
-                 r.params.inv_precision, r.params.combine, r.params.form, r.params.eps};
+                 r.params.inv_precision, r.params.combine, r.params.form,
+                 r.params.compensated, r.params.eps};
     auto it = cache.find(key);
     CacheEntry *e = nullptr;
     cudaError_t err = cudaSuccess;
@@ -190,6 +191,7 @@ struct hgf_server {
       g.inv_precision = r.params.inv_precision;
       g.combine = r.params.combine;
       g.form = r.params.form;
+      g.compensated = r.params.compensated;
       const size_t HW = (size_t)r.H * r.W;
       g.rec = (float *)ent->base;
       g.img = g.rec + record_total_floats(r.H, r.W, g.n, g.r);
@@ -349,7 +351,8 @@ hgf_status hgf_serve_submit(hgf_server *s, const hgf_request *req, uint64_t *id)
       (r.cost_dtype != HGF_F32 && r.cost_dtype != HGF_BF16 && r.cost_dtype != HGF_F16) ||
       (r.params.inv_precision != HGF_F64 && r.params.inv_precision != HGF_F32) ||
       (r.params.combine != HGF_COMBINE_ALPHA && r.params.combine != HGF_COMBINE_W3) ||
-      (r.params.form != HGF_FORM_CENTRED && r.params.form != HGF_FORM_PAPER))
+      (r.params.form != HGF_FORM_CENTRED && r.params.form != HGF_FORM_PAPER) ||
+      (r.params.compensated != 0 && r.params.compensated != 1))
     return HGF_EINVAL;
   const int n = hgf_num_channels(r.C, r.params.degree, r.params.basis);
   if (n < 1 || !aggregate_supported(n)) return HGF_EUNSUPPORTED;

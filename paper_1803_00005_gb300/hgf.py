@@ -51,7 +51,8 @@ class HGFError(RuntimeError):
 class hgf_params(ctypes.Structure):
     _fields_ = [("degree", ctypes.c_int), ("basis", ctypes.c_int), ("r", ctypes.c_int),
                 ("eps", ctypes.c_double), ("inv_precision", ctypes.c_int),
-                ("combine", ctypes.c_int), ("form", ctypes.c_int)]
+                ("combine", ctypes.c_int), ("form", ctypes.c_int),
+                ("compensated", ctypes.c_int)]
 
 
 class hgf_cost_params(ctypes.Structure):
@@ -187,13 +188,14 @@ def _require_cuda(t, name):
 
 
 def make_params(degree=1, r=4, eps=1e-4, basis="monomial", inv_precision="f64", combine="alpha",
-                form="centred"):
+                form="centred", compensated=False):
     """form: "centred" (Sec. 5.1; eps in units of window means) or "paper" (G_0 = 1, uncentred
-    window sums, lambda = eps in units of window sums; Sec. 3-4)."""
+    window sums, lambda = eps in units of window sums; Sec. 3-4). compensated: Kahan-compensated
+    running sums in the strip kernels."""
     return hgf_params(degree=int(degree), basis=BASIS_CODES[basis], r=int(r), eps=float(eps),
                       inv_precision=DTYPE_CODES[inv_precision],
                       combine=HGF_COMBINE_ALPHA if combine == "alpha" else HGF_COMBINE_W3,
-                      form=FORM_CODES[form])
+                      form=FORM_CODES[form], compensated=1 if compensated else 0)
 
 
 # ------------------------------------------------------------------ entry points, same names

@@ -27,14 +27,16 @@ def cost_tensor(torch, cost, dtype):
 
 
 def run_path(ctx, guidance, cost, dtype, degree, r, eps, basis="monomial", plain=False,
-             inv_precision="f64", combine="alpha", want_filtered=True, form="centred"):
+             inv_precision="f64", combine="alpha", want_filtered=True, form="centred",
+             compensated=False):
     torch = torch_cuda()
     from paper_1803_00005_gb300 import hgf
     img = torch.from_numpy(np.ascontiguousarray(guidance, dtype=np.float32)).cuda()
     c = cost_tensor(torch, cost, dtype)
     L, H, W = cost.shape
     params = hgf.make_params(degree=degree, r=r, eps=eps, basis=basis,
-                             inv_precision=inv_precision, combine=combine, form=form)
+                             inv_precision=inv_precision, combine=combine, form=form,
+                             compensated=compensated)
     g = hgf.hgf_prepare(ctx, img, params)
     try:
         filt = torch.empty((L, H, W), dtype=torch.float32, device="cuda") if want_filtered else None

@@ -242,3 +242,23 @@ def test_results_independent_of_label_chunking(ctx):
             assert np.array_equal(got[0], base[0]) and np.array_equal(got[1], base[1])
     finally:
         hgf.hgf_set_tuning(ctx)
+
+
+@pytest.mark.parametrize("degree,r", [(2, 9), (1, 4), (3, 4)])
+def test_compensated_running_sums(ctx, degree, r, capsys):
+    """Kahan-compensated running sums (hgf_params.compensated): the same tolerance holds, and the
+    RMS error against the float64 oracle stays that of the uncompensated path (within 20%): the
+    vertical running sums are not the dominant rounding source (the prefix-scan differences and
+    the float32 mat-vec are), so compensation moves the maximum error up or down by rounding
+    chance and leaves the RMS error where it was. Both are printed."""
+    case, ref = oracle_case(300, 170, 7, 61, degree=degree, r=r, eps=1e-4)
+    q, labels, best = run_path(ctx, case.guidance, case.cost, "f32", degree, r, 1e-4,
+                               compensated=True)
+    check_against_oracle(q, labels, best, ref)
+    q0, _, _ = run_path(ctx, case.guidance, case.cost, "f32", degree, r, 1e-4)
+    scale = float(np.max(np.abs(ref)))
+    rms = [float(np.sqrt(np.mean((x - ref) ** 2))) / scale for x in (q0, q)]
+    with capsys.disabled():
+        print(f"\ndegree {degree} r {r}: max {normwise(q0, ref):.2e} -> {normwise(q, ref):.2e}, "
+              f"rms {rms[0]:.2e} -> {rms[1]:.2e} (plain -> compensated)")
+    assert rms[1] <= 1.2 * rms[0]

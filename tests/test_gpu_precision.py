@@ -1,6 +1,6 @@
 """Precision variants on the 1400x1100 / 256-label / n=9 / r=9 workload: cost storage float32,
-bfloat16, float16 (float32 accumulation) and the covariance assembly + inverse in float64 vs
-float32. Each variant's error is measured against the float64 oracle on sampled pixels (the oracle
+bfloat16, float16 (float32 accumulation), the covariance assembly + inverse in float64 vs
+float32, and Kahan-compensated running sums. Each variant's error is measured against the float64 oracle on sampled pixels (the oracle
 runs on the exact crop each sampled output depends on), both against the oracle fed the same
 rounded costs (the kernels' own error) and against the oracle fed the float32 costs (adding the
 storage rounding). The table is printed (pytest -s) and the bounds below are asserted."""
@@ -47,9 +47,10 @@ def test_precision_variants(workload, capsys):
             exact = synth.from_dtype(stored, dtype)
             ref_same = ref32 if dtype == "f32" else O.filter_at(guid, exact, R, EPS, DEG, pts)
             cost = cost_tensor(torch, stored, dtype)
-            for prec in ("f64", "f32"):
+            for prec, comp in (("f64", False), ("f32", False), ("f64", True)):
                 g = hgf.hgf_prepare(ctx, img, hgf.make_params(degree=DEG, r=R, eps=EPS,
-                                                              inv_precision=prec))
+                                                              inv_precision=prec,
+                                                              compensated=comp))
                 q = torch.empty((L, H, W), device="cuda")
                 lab = torch.empty((H, W), dtype=torch.int32, device="cuda")
                 hgf.hgf_aggregate(ctx, g, cost, filtered=q, labels=lab)
@@ -62,17 +63,17 @@ def test_precision_variants(workload, capsys):
                 ol, _, om = O.wta(ref32[:, :, None])
                 gl = np.array([int(lab[y, x]) for y, x in pts])
                 agree = float(np.mean(gl == ol[:, 0]))
-                rows.append((dtype, prec, e_same, e_store, agree))
+                rows.append((dtype, prec + ("+kahan" if comp else ""), e_same, e_store, agree))
                 del q
     finally:
         hgf.hgf_destroy(ctx)
     with capsys.disabled():
-        print("\ncost   inverse  err vs oracle(same costs)  err vs oracle(f32 costs)  "
+        print("\ncost   inverse+sums  err vs oracle(same costs)  err vs oracle(f32 costs)  "
               "label agreement (sampled, vs f32 oracle)")
         for d, p, a, b, c in rows:
-            print(f"{d:6s} {p:8s} {a:24.2e}  {b:24.2e}  {c:8.3f}")
+            print(f"{d:6s} {p:12s} {a:24.2e}  {b:24.2e}  {c:8.3f}")
     for d, p, a, b, c in rows:
-        if p == "f64":
+        if p.startswith("f64"):
             assert a <= 1e-4, (d, p, a)       # the kernels' own error meets the tolerance
         else:
             assert a <= 5e-2, (d, p, a)       # float32 inverse: reported, larger
