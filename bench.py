@@ -95,6 +95,8 @@ def parse():
     ap.add_argument("--impl", choices=["fused", "plain", "reference"], default="fused")
     ap.add_argument("--workload", choices=list(WORKLOADS), default="quarter")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--inv-precision", choices=["f64", "df64", "f32"], default="f64",
+                    help="arithmetic of the covariance assembly + inverse")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-crop", type=int, nargs=2, default=(225, 188),
                     help="width height of the centred crop the CPU baseline runs on")
@@ -204,7 +206,7 @@ def inverse_arm(args):
         S = synth.pack_upper(synth.gram_batch_torch(args.count, n, seed=11 + n))
         out = torch.empty_like(S)
         for method in ("prop1", "cholesky"):
-            for prec in ("f64", "f32"):
+            for prec in ("f64", "df64", "f32"):
                 for _ in range(max(3, args.warmup)):
                     hgf.hgf_batched_inverse(ctx, S, n, 0.05, method, prec, out)
                 ms = []
@@ -232,7 +234,7 @@ def inverse_arm(args):
                                    r["method"] == "cholesky" and r["precision"] == prec) /
              next(r["ms"] for r in table if r["n"] == n and r["method"] == "prop1" and
                   r["precision"] == prec)
-             for n in (3, 6, 9, 19) for prec in ("f64", "f32")}
+             for n in (3, 6, 9, 19) for prec in ("f64", "df64", "f32")}
     line = dict(metric="matrices/s, batched (lambda E + S)^-1, Prop. 1, n=9, float64",
                 value=key["matrices_per_s"], unit="matrices/s", n_gpus=1, steps=reps,
                 warmup=max(3, args.warmup), ms_per_step=key["ms"], higher_is_better=True,
@@ -583,7 +585,8 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     ctx = hgf.hgf_create(local_rank)
-    params = hgf.make_params(degree=w["degree"], r=w["r"], eps=w["eps"])
+    params = hgf.make_params(degree=w["degree"], r=w["r"], eps=w["eps"],
+                             inv_precision=args.inv_precision)
     g = hgf.hgf_prepare(ctx, img, params)
     agg = hgf.hgf_aggregate_plain if args.impl == "plain" else hgf.hgf_aggregate
 
@@ -720,7 +723,7 @@ def main():
         line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
                     warmup=args.warmup, ms_per_step=1e3 * t_max / args.steps,
                     higher_is_better=True, scaling="weak", vs_baseline=None,
-                    dtype="f32 (f64 inverse)", data="synthetic",
+                    dtype=f"f32 ({args.inv_precision} inverse)", data="synthetic",
                     impl=args.impl,
                     config=dict(workload=w["name"], parallelism=f"replicas x{world}",
                                 l2="256 MiB buffer written between timed steps",

@@ -43,7 +43,10 @@ typedef enum {
   HGF_EUNSUPPORTED = 7   /* valid but not supported (e.g. n > 19) */
 } hgf_status;
 
-typedef enum { HGF_F32 = 0, HGF_BF16 = 1, HGF_F16 = 2, HGF_F64 = 3 } hgf_dtype;
+/* HGF_DF64 is an arithmetic precision only (hgf_params.inv_precision, hgf_batched_inverse):
+ * double-float, the unevaluated sum of two float32 numbers (about 48 significant bits), built from
+ * float32 operations that GB300 runs at 64 times its float64 rate. */
+typedef enum { HGF_F32 = 0, HGF_BF16 = 1, HGF_F16 = 2, HGF_F64 = 3, HGF_DF64 = 4 } hgf_dtype;
 
 /* Guidance basis (Sec. 4.2). MONOMIAL: every monomial of degree 1..d of the C input channels,
  * degree-major then lexicographic (R, G, B, RR, RG, RB, GG, GB, BB, RRR, ...), n = C(C+d,d) - 1.
@@ -71,7 +74,8 @@ typedef struct {
   int basis;          /* hgf_basis */
   int r;              /* window radius r >= 0: (2r+1)^2 box (Sec. 6 uses r = 7) */
   double eps;         /* regulariser eps > 0 (lambda); units depend on `form` */
-  int inv_precision;  /* HGF_F64 (default) or HGF_F32: precision of Sigma assembly + recursion */
+  int inv_precision;  /* precision of the covariance assembly + recursion: HGF_F64 (default,
+                       * native float64), HGF_DF64 (double-float) or HGF_F32 */
   int combine;        /* hgf_combine */
   int form;           /* hgf_form (0 = CENTRED) */
   int compensated;    /* 1: Kahan-compensated vertical running sums in the guidance-moment and
@@ -335,7 +339,7 @@ hgf_status hgf_refine_lr(hgf_ctx *ctx, const int32_t *disp_left, const int32_t *
  *           [e * count + i]. The caller owns both; they must not overlap.
  *   method: HGF_INV_PROP1 (Prop. 1 recursion with lambda, inverse = -lambda alpha) or
  *           HGF_INV_CHOLESKY (Cholesky factor of lambda E + S, inverse from the factor).
- *   precision: HGF_F64 or HGF_F32 arithmetic (input and output stay float64).
+ *   precision: HGF_F64, HGF_DF64 or HGF_F32 arithmetic (input and output stay float64).
  * Enqueued on `stream`. HGF_EINVAL: NULL pointers, count < 1, lambda <= 0, unknown method or
  * precision; HGF_EUNSUPPORTED: n not built. S_i must be positive semidefinite (Gram matrices);
  * otherwise the result is unspecified (no error is detected). */

@@ -99,8 +99,9 @@ hgf_status check_params(hgf_ctx *ctx, int C, int H, int W, const hgf_params *p, 
   if (p->degree < 1) return set_err(ctx, HGF_EINVAL, "degree must be >= 1");
   if (p->basis != HGF_BASIS_MONOMIAL && p->basis != HGF_BASIS_POWERS)
     return set_err(ctx, HGF_EINVAL, "unknown basis %d", p->basis);
-  if (p->inv_precision != HGF_F64 && p->inv_precision != HGF_F32)
-    return set_err(ctx, HGF_EINVAL, "inv_precision must be HGF_F64 or HGF_F32");
+  if (p->inv_precision != HGF_F64 && p->inv_precision != HGF_F32 &&
+      p->inv_precision != HGF_DF64)
+    return set_err(ctx, HGF_EINVAL, "inv_precision must be HGF_F64, HGF_DF64 or HGF_F32");
   if (p->combine != HGF_COMBINE_ALPHA && p->combine != HGF_COMBINE_W3)
     return set_err(ctx, HGF_EINVAL, "unknown combine %d", p->combine);
   if (p->form != HGF_FORM_CENTRED && p->form != HGF_FORM_PAPER)
@@ -622,8 +623,8 @@ hgf_status hgf_batched_inverse(hgf_ctx *ctx, const double *S, int count, int n, 
   if (!(lambda > 0.0)) return set_err(ctx, HGF_EINVAL, "lambda must be > 0");
   if (method != HGF_INV_PROP1 && method != HGF_INV_CHOLESKY)
     return set_err(ctx, HGF_EINVAL, "unknown method %d", method);
-  if (precision != HGF_F64 && precision != HGF_F32)
-    return set_err(ctx, HGF_EINVAL, "precision must be HGF_F64 or HGF_F32");
+  if (precision != HGF_F64 && precision != HGF_F32 && precision != HGF_DF64)
+    return set_err(ctx, HGF_EINVAL, "precision must be HGF_F64, HGF_DF64 or HGF_F32");
   if (!aggregate_supported(n)) return set_err(ctx, HGF_EUNSUPPORTED, "n = %d is not built", n);
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   cudaError_t e = launch_batched_inverse(S, count, n, lambda, method, precision, out,

@@ -6,6 +6,7 @@
 // entry e of matrix i is at [e * count + i], so consecutive threads touch consecutive addresses.
 // Input and output are float64; T is the arithmetic precision.
 #include "hgf_internal.cuh"
+#include "hgf_df64.cuh"
 #include "hgf_prop1.cuh"
 
 namespace hgf {
@@ -125,6 +126,7 @@ cudaError_t launch_t(const double *S, int count, int n, double lambda, int metho
 cudaError_t launch_batched_inverse(const double *S, int count, int n, double lambda, int method,
                                    int precision, double *out, cudaStream_t s, Profiler *prof) {
   if (precision == HGF_F32) return launch_t<float>(S, count, n, lambda, method, out, s, prof);
+  if (precision == HGF_DF64) return launch_t<df64>(S, count, n, lambda, method, out, s, prof);
   return launch_t<double>(S, count, n, lambda, method, out, s, prof);
 }
 

@@ -8,6 +8,7 @@
 // sums of 2r+1 terms per axis; the assembly Sigma = A(GG^T) - mu mu^T and the recursion run in the
 // precision chosen by hgf_params.inv_precision (float64 by default).
 #include "hgf_basis.cuh"
+#include "hgf_df64.cuh"
 #include "hgf_prop1.cuh"
 #include "hgf_scan.cuh"
 
@@ -603,8 +604,9 @@ cudaError_t launch_prepare(hgf_guidance *g, const float *img, void *ws, size_t w
       k_moment_cols<<<grid, 128, 0, s>>>(rows, H, W, g->r, mom);
     }
   }
-  bool ok = g->inv_precision == HGF_F32 ? launch_inverse_n<float>(mom, g, s, prof)
-                                        : launch_inverse_n<double>(mom, g, s, prof);
+  bool ok = g->inv_precision == HGF_F32    ? launch_inverse_n<float>(mom, g, s, prof)
+            : g->inv_precision == HGF_DF64 ? launch_inverse_n<df64>(mom, g, s, prof)
+                                           : launch_inverse_n<double>(mom, g, s, prof);
   if (!ok) return cudaErrorInvalidValue;
   return cudaGetLastError();
 }

@@ -349,7 +349,8 @@ hgf_status hgf_serve_submit(hgf_server *s, const hgf_request *req, uint64_t *id)
   if (!r.img || !r.cost || !r.labels || r.L < 1 || r.H < 1 || r.W < 1 ||
       (r.C != 1 && r.C != 3) || r.params.r < 0 || !(r.params.eps > 0.0) ||
       (r.cost_dtype != HGF_F32 && r.cost_dtype != HGF_BF16 && r.cost_dtype != HGF_F16) ||
-      (r.params.inv_precision != HGF_F64 && r.params.inv_precision != HGF_F32) ||
+      (r.params.inv_precision != HGF_F64 && r.params.inv_precision != HGF_F32 &&
+       r.params.inv_precision != HGF_DF64) ||
       (r.params.combine != HGF_COMBINE_ALPHA && r.params.combine != HGF_COMBINE_W3) ||
       (r.params.form != HGF_FORM_CENTRED && r.params.form != HGF_FORM_PAPER) ||
       (r.params.compensated != 0 && r.params.compensated != 1))

@@ -17,13 +17,14 @@ HGF_OK, HGF_EINVAL, HGF_ENOMEM, HGF_ECUDA, HGF_ETIMEOUT, HGF_EBUSY, HGF_EAGAIN, 
     HGF_EUNSUPPORTED = range(8)
 STATUS_NAMES = ["HGF_OK", "HGF_EINVAL", "HGF_ENOMEM", "HGF_ECUDA", "HGF_ETIMEOUT", "HGF_EBUSY",
                 "HGF_EAGAIN", "HGF_EUNSUPPORTED"]
-HGF_F32, HGF_BF16, HGF_F16, HGF_F64 = range(4)
+HGF_F32, HGF_BF16, HGF_F16, HGF_F64, HGF_DF64 = range(5)
 HGF_BASIS_MONOMIAL, HGF_BASIS_POWERS = range(2)
 HGF_COMBINE_ALPHA, HGF_COMBINE_W3 = range(2)
 HGF_FORM_CENTRED, HGF_FORM_PAPER = range(2)
 HGF_INV_PROP1, HGF_INV_CHOLESKY = range(2)
 
-DTYPE_CODES = {"f32": HGF_F32, "bf16": HGF_BF16, "f16": HGF_F16, "f64": HGF_F64}
+DTYPE_CODES = {"f32": HGF_F32, "bf16": HGF_BF16, "f16": HGF_F16, "f64": HGF_F64,
+               "df64": HGF_DF64}
 BASIS_CODES = {"monomial": HGF_BASIS_MONOMIAL, "powers": HGF_BASIS_POWERS}
 FORM_CODES = {"centred": HGF_FORM_CENTRED, "paper": HGF_FORM_PAPER}
 

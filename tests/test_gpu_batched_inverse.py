@@ -4,7 +4,8 @@ Cholesky solves on CPU), on seeded Gram matrices S_i = sum_k x_k x_k^T of 25 sam
 x_k ~ U[0,1]^n.
 
 Bound per matrix: max|X - X*| / max|X*| <= 10 n u (1 + ||S||/lambda) cond(lambda E + S), with u
-the unit roundoff of the arithmetic (2^-53 for float64, 2^-24 for float32): the recursion's error
+the unit roundoff of the arithmetic (2^-53 for float64, 2^-47 for double-float pairs of float32,
+2^-24 for float32): the recursion's error
 grows with ||S||/lambda (its gamma denominators) times the conditioning of the solve."""
 import numpy as np
 import pytest
@@ -43,7 +44,7 @@ def test_batched_inverse_parity(ctx, n, lam, capsys):
     Sd = torch.from_numpy(synth.pack_upper(S)).cuda()
     rows, cols = np.triu_indices(n)
     for method in ("prop1", "cholesky"):
-        for prec, u in (("f64", 2.0 ** -53), ("f32", 2.0 ** -24)):
+        for prec, u in (("f64", 2.0 ** -53), ("df64", 2.0 ** -47), ("f32", 2.0 ** -24)):
             out = hgf.hgf_batched_inverse(ctx, Sd, n, lam, method=method, precision=prec)
             torch.cuda.synchronize()
             got = out.cpu().numpy()                            # (P, count)

@@ -262,3 +262,19 @@ def test_compensated_running_sums(ctx, degree, r, capsys):
         print(f"\ndegree {degree} r {r}: max {normwise(q0, ref):.2e} -> {normwise(q, ref):.2e}, "
               f"rms {rms[0]:.2e} -> {rms[1]:.2e} (plain -> compensated)")
     assert rms[1] <= 1.2 * rms[0]
+
+
+@pytest.mark.parametrize("degree,r", [(2, 9), (3, 4), (1, 4)])
+def test_double_float_inverse(ctx, degree, r, capsys):
+    """The covariance assembly + Prop. 1 recursion in double-float (inv_precision = HGF_DF64,
+    pairs of float32, about 48 bits): the same tolerance as native float64, and an error within
+    10% (plus 1e-7) of the float64 path's, since both round the inverse to float32 records."""
+    case, ref = oracle_case(300, 170, 7, 61, degree=degree, r=r, eps=1e-4)
+    q, labels, best = run_path(ctx, case.guidance, case.cost, "f32", degree, r, 1e-4,
+                               inv_precision="df64")
+    check_against_oracle(q, labels, best, ref)
+    q0, _, _ = run_path(ctx, case.guidance, case.cost, "f32", degree, r, 1e-4)
+    with capsys.disabled():
+        print(f"\ndegree {degree} r {r}: float64 {normwise(q0, ref):.2e}, "
+              f"double-float {normwise(q, ref):.2e}")
+    assert normwise(q, ref) <= 1.1 * normwise(q0, ref) + 1e-7
