@@ -115,13 +115,17 @@ __global__ void __launch_bounds__(kMeanThreads) k_mean_partial(const float *__re
   }
 }
 
+// One warp per channel: lane l sums partials l, l + 32, ..., then a fixed shuffle tree (the
+// order is fixed, so every call gives the same shift).
 __global__ void k_mean_final(const double *__restrict__ partial, int nblk, int n, int HW,
                              float *__restrict__ shift) {
-  int i = threadIdx.x;
+  const int i = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (i >= n) return;
   double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += partial[b * n + i];
-  shift[i] = (float)(s / HW);
+  for (int b = lane; b < nblk; b += 32) s += partial[b * n + i];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if (lane == 0) shift[i] = (float)(s / HW);
 }
 
 // Shifted guidance planes G_i - c_i (used by the moment sums and the plain form).
@@ -142,20 +146,24 @@ __global__ void k_shifted_guidance(const float *__restrict__ img, const float *_
 }
 
 // ------------------------------------------------------------------ moment window sums (strips)
-// The window sums of every moment channel in one pass, for n <= 9: a CTA walks down a band of
-// rows over a 128-column strip (one thread per column, 2r halo columns), keeps the vertical
-// window sums of the M = n + n(n+1)/2 channels in registers (adding the entering row's
-// products, subtracting those of the row leaving the window, re-read from L2), and forms the
-// horizontal window sums by prefix scans of shared rows. Channel m < n is G_m; m >= n is the
-// pair (i, j), i <= j, of the packed upper triangle.
-template <int NG, bool COMP>
-__global__ void __launch_bounds__(kStripThreads) k_moments(const float *__restrict__ G, int H,
-                                                           int W, int r, int band_rows,
-                                                           float *__restrict__ mom) {
+// The window sums of the moment channels for n <= 9: a CTA walks down a band of rows over a
+// 128-column strip (one thread per column, 2r halo columns), keeps the vertical window sums of its
+// channels in registers (adding the entering row's values, subtracting those of the row leaving
+// the window, re-read from L2), and forms the horizontal window sums by prefix scans of shared
+// rows. Channel m < n is G_m; m >= n is the pair (i, j), i <= j, of the packed upper triangle.
+// The M = n + n(n+1)/2 channels are split into groups of at most kMomentGroup (grid z), so that a
+// small image still gives enough CTAs and each thread holds fewer sums.
+constexpr int kMomentGroup = 18;
+
+template <int NG, bool COMP, int GRP>
+__device__ __forceinline__ void moments_group(const float *__restrict__ G, int H, int W, int r,
+                                              int band_rows, float *__restrict__ mom,
+                                              float *smem) {
   using namespace strip;
   constexpr int M = NG + NG * (NG + 1) / 2;
-  constexpr int RPW = (M + NT / 32 - 1) / (NT / 32);
-  extern __shared__ __align__(16) float smem[];  // two scan buffers of M rows, alternate rows
+  constexpr int M0 = GRP * kMomentGroup;
+  constexpr int MG = (M - M0) < kMomentGroup ? (M - M0) : kMomentGroup;
+  constexpr int RPW = (MG + NT / 32 - 1) / (NT / 32);
   const size_t HW = (size_t)H * W;
   const int t = threadIdx.x;
   const int TW = NT - 2 * r;
@@ -166,7 +174,7 @@ __global__ void __launch_bounds__(kStripThreads) k_moments(const float *__restri
   const int Y1 = min(H, Y0 + band_rows);
   const int add_lo = max(0, Y0 - r);
   const int s_begin = Y0 - r, s_end = Y1 + r;
-  for (int i = t; i < 2 * M; i += NT) smem[i * kRowStride + 3] = 0.f;
+  for (int i = t; i < 2 * MG; i += NT) smem[i * kRowStride + 3] = 0.f;
 
   auto ld_new = [&](int row, float *v) {
     if (col_ok && row >= 0 && row < H) {
@@ -187,11 +195,12 @@ __global__ void __launch_bounds__(kStripThreads) k_moments(const float *__restri
   ld_new(s_begin + 1, pb);
   ld_old(s_begin - 2 * r - 1, oa);
   ld_old(s_begin - 2 * r, ob);
-  float V[M], Vc[COMP ? M : 1];  // running sums and (COMP) their Kahan compensation terms
+  float V[MG], Vc[COMP ? MG : 1];  // running sums and (COMP) their Kahan compensation terms
 #pragma unroll
-  for (int m = 0; m < M; ++m) V[m] = 0.f;
+  for (int m = 0; m < MG; ++m) V[m] = 0.f;
 #pragma unroll
-  for (int m = 0; m < (COMP ? M : 1); ++m) Vc[m] = 0.f;
+  for (int m = 0; m < (COMP ? MG : 1); ++m) Vc[m] = 0.f;
+  // V[m] += x for channel M0 + m (compensated in the COMP instantiation)
   auto acc = [&](int m, float x) {
     if constexpr (COMP) {
       const float y = x - Vc[m];
@@ -202,6 +211,26 @@ __global__ void __launch_bounds__(kStripThreads) k_moments(const float *__restri
       V[m] += x;
     }
   };
+  // adds sign * (every channel of this group) at a row with guidance values g; the loops unroll
+  // completely, so the channel tests and indices are compile-time constants
+  auto update = [&](const float *g, float sign) {
+#pragma unroll
+    for (int i = 0; i < NG; ++i)
+      if (i >= M0 && i < M0 + MG) acc(i - M0, sign * g[i]);
+#pragma unroll
+    for (int i = 0; i < NG; ++i) {
+#pragma unroll
+      for (int j = i; j < NG; ++j) {
+        const int c = NG + tri_index(NG, i, j);
+        if (c >= M0 && c < M0 + MG) {
+          if constexpr (COMP)
+            acc(c - M0, sign * g[i] * g[j]);
+          else
+            V[c - M0] = fmaf(sign * g[i], g[j], V[c - M0]);
+        }
+      }
+    }
+  };
 
   // three-buffer rotation: row s + 2 (and the row leaving two steps later) load while row s works
   auto step = [&](const int s, const float *cur, float *nxt, const float *cur_o, float *nxt_o) {
@@ -209,46 +238,24 @@ __global__ void __launch_bounds__(kStripThreads) k_moments(const float *__restri
     ld_new(s + 2, nxt);
     ld_old(s + 1 - 2 * r, nxt_o);
     if (col_ok) {
-      if (s - 2 * r - 1 >= add_lo) {
-#pragma unroll
-        for (int i = 0; i < NG; ++i) {
-          acc(i, -cur_o[i]);
-#pragma unroll
-          for (int j = i; j < NG; ++j) {
-            if constexpr (COMP)
-              acc(NG + tri_index(NG, i, j), -cur_o[i] * cur_o[j]);
-            else
-              V[NG + tri_index(NG, i, j)] = fmaf(-cur_o[i], cur_o[j], V[NG + tri_index(NG, i, j)]);
-          }
-        }
-      }
-      if (s >= 0 && s < H) {
-#pragma unroll
-        for (int i = 0; i < NG; ++i) {
-          acc(i, cur[i]);
-#pragma unroll
-          for (int j = i; j < NG; ++j) {
-            if constexpr (COMP)
-              acc(NG + tri_index(NG, i, j), cur[i] * cur[j]);
-            else
-              V[NG + tri_index(NG, i, j)] = fmaf(cur[i], cur[j], V[NG + tri_index(NG, i, j)]);
-          }
-        }
-      }
+      if (s - 2 * r - 1 >= add_lo) update(cur_o, -1.f);
+      if (s >= 0 && s < H) update(cur, 1.f);
     }
     const int y2 = s - r;
     if (y2 < Y0) return;  // warm-up rows (uniform per CTA)
-    float *sA = smem + ((y2 - Y0) & 1) * M * kRowStride;
+    float *sA = smem + ((y2 - Y0) & 1) * MG * kRowStride;
 #pragma unroll
-    for (int m = 0; m < M; ++m) sA[m * kRowStride + 4 + t] = COMP ? V[m] - Vc[COMP ? m : 0] : V[m];
+    for (int m = 0; m < MG; ++m)
+      sA[m * kRowStride + 4 + t] = COMP ? V[m] - Vc[COMP ? m : 0] : V[m];
     __syncthreads();
-    scan_rows<RPW>(sA, M);
+    scan_rows<RPW>(sA, MG);
     __syncthreads();
     const int x = x0 + t;
     if (t < TW && x < W) {
       const size_t pix = (size_t)y2 * W + x;
 #pragma unroll
-      for (int m = 0; m < M; ++m) mom[(size_t)m * HW + pix] = window(sA + m * kRowStride, t, r);
+      for (int m = 0; m < MG; ++m)
+        mom[(size_t)(M0 + m) * HW + pix] = window(sA + m * kRowStride, t, r);
     }
   };
   for (int s = s_begin; s < s_end; s += 3) {
@@ -259,10 +266,35 @@ __global__ void __launch_bounds__(kStripThreads) k_moments(const float *__restri
 }
 
 template <int NG, bool COMP>
+__global__ void __launch_bounds__(kStripThreads) k_moments(const float *__restrict__ G, int H,
+                                                           int W, int r, int band_rows,
+                                                           float *__restrict__ mom) {
+  constexpr int M = NG + NG * (NG + 1) / 2;
+  extern __shared__ __align__(16) float smem[];  // two scan buffers of a group's rows
+  switch (blockIdx.z) {  // uniform per CTA
+    case 0:
+      moments_group<NG, COMP, 0>(G, H, W, r, band_rows, mom, smem);
+      break;
+    case 1:
+      if constexpr (M > kMomentGroup) moments_group<NG, COMP, 1>(G, H, W, r, band_rows, mom, smem);
+      break;
+    case 2:
+      if constexpr (M > 2 * kMomentGroup)
+        moments_group<NG, COMP, 2>(G, H, W, r, band_rows, mom, smem);
+      break;
+    default:
+      break;
+  }
+}
+
+template <int NG, bool COMP>
 cudaError_t launch_moments_strip(const float *G, int H, int W, int r, int num_sms, float *mom,
                                  cudaStream_t s, Profiler *prof) {
   constexpr int M = NG + NG * (NG + 1) / 2;
-  const size_t sm = sizeof(float) * 2 * M * strip::kRowStride;
+  constexpr int groups = (M + kMomentGroup - 1) / kMomentGroup;
+  static_assert(groups <= 3, "k_moments dispatches three channel groups at most");
+  constexpr int MG = M < kMomentGroup ? M : kMomentGroup;
+  const size_t sm = sizeof(float) * 2 * MG * strip::kRowStride;
   cudaError_t e = cudaSuccess;
   if (sm > 48 * 1024) {
     e = cudaFuncSetAttribute(k_moments<NG, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -285,14 +317,14 @@ cudaError_t launch_moments_strip(const float *G, int H, int W, int r, int num_sm
   int rows = H;
   for (int bands = 1; bands <= std::max(1, H / std::max(8, 2 * r)); ++bands) {
     const int rw = (H + bands - 1) / bands;
-    const long long ctas = (long long)strips * ((H + rw - 1) / rw);
+    const long long ctas = (long long)strips * groups * ((H + rw - 1) / rw);
     const long long cost = ((ctas + resident - 1) / resident) * (rw + 2 * r);
     if (best_cost < 0 || cost < best_cost) {
       best_cost = cost;
       rows = rw;
     }
   }
-  dim3 grid(strips, (H + rows - 1) / rows);
+  dim3 grid(strips, (H + rows - 1) / rows, groups);
   LaunchScope ls(prof, "k_moments", s);
   k_moments<NG, COMP><<<grid, kStripThreads, sm, s>>>(G, H, W, r, rows, mom);
   return cudaGetLastError();
@@ -567,7 +599,7 @@ cudaError_t launch_prepare(hgf_guidance *g, const float *img, void *ws, size_t w
     }
     {
       LaunchScope ls(prof, "k_mean_final", s);
-      k_mean_final<<<1, 32, 0, s>>>(partial, kMeanBlocks, n, HW, g->shift);
+      k_mean_final<<<1, 32 * n, 0, s>>>(partial, kMeanBlocks, n, HW, g->shift);
     }
     {
       LaunchScope ls(prof, "k_shifted_guidance", s);
