@@ -169,7 +169,9 @@ hgf_status hgf_wta(hgf_ctx *ctx, const void *filtered, int dtype, int L, int H, 
 /* End to end from host memory: copies img (host, C x H x W float32) and cost (host, L x H x W of
  * cost_dtype) to the device, prepares the guidance, aggregates with WTA and copies labels (host
  * int32 H x W, may be NULL) and best (host float32 H x W, may be NULL) back; returns after the
- * results are in host memory. Host buffers may be pageable or pinned (pinned is faster). */
+ * results are in host memory. Host buffers may be pageable or pinned (pinned is faster). The cost
+ * volume is uploaded on a second, library-owned stream while the guidance precompute runs on
+ * `stream`; the aggregation waits for the upload. */
 hgf_status hgf_filter_host(hgf_ctx *ctx, const float *img, int C, int H, int W,
                            const hgf_params *params, const void *cost, int cost_dtype, int L,
                            int32_t *labels, float *best, void *stream);

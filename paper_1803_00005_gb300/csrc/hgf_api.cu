@@ -283,6 +283,9 @@ hgf_status hgf_destroy(hgf_ctx *ctx) {
   for (Workspace *w : {&ctx->ws_prepare, &ctx->ws_coef, &ctx->ws_keys, &ctx->ws_plain,
                        &ctx->ws_io, &ctx->ws_grad})
     if (w->ptr) cudaFree(w->ptr);
+  if (ctx->io_fork) cudaEventDestroy(ctx->io_fork);
+  if (ctx->io_done) cudaEventDestroy(ctx->io_done);
+  if (ctx->io_stream) cudaStreamDestroy(ctx->io_stream);
   delete ctx;
   return HGF_OK;
 }
@@ -309,6 +312,7 @@ hgf_status hgf_make_guidance(hgf_ctx *ctx, const float *img, int C, int H, int W
 
 hgf_status hgf_prepare(hgf_ctx *ctx, const float *img, int C, int H, int W,
                        const hgf_params *params, void *stream, hgf_guidance **out) {
+  NvtxRange nvtx_range("hgf_prepare");
   hgf_status st = enter(ctx);
   if (st != HGF_OK) return st;
   if (!out) return set_err(ctx, HGF_EINVAL, "out is NULL");
@@ -382,6 +386,7 @@ hgf_status hgf_set_tuning(hgf_ctx *ctx, const hgf_tuning *t) {
 hgf_status hgf_autotune(hgf_ctx *ctx, const hgf_guidance *g, const void *cost, int cost_dtype,
                         int L, int32_t *labels, int reps, hgf_tuning *best, int *ncand,
                         void *stream) {
+  NvtxRange nvtx_range("hgf_autotune");
   hgf_status st = enter(ctx);
   if (st != HGF_OK) return st;
   st = check_outputs(ctx, g, cost, cost_dtype, L, nullptr, HGF_F32, labels, nullptr);
@@ -434,6 +439,7 @@ hgf_status hgf_autotune(hgf_ctx *ctx, const hgf_guidance *g, const void *cost, i
 hgf_status hgf_aggregate(hgf_ctx *ctx, const hgf_guidance *g, const void *cost, int cost_dtype,
                          int L, void *filtered, int filtered_dtype, int32_t *labels, float *best,
                          void *stream) {
+  NvtxRange nvtx_range("hgf_aggregate");
   hgf_status st = enter(ctx);
   if (st != HGF_OK) return st;
   st = check_outputs(ctx, g, cost, cost_dtype, L, filtered, filtered_dtype, labels, best);
@@ -446,6 +452,7 @@ hgf_status hgf_aggregate(hgf_ctx *ctx, const hgf_guidance *g, const void *cost, 
 hgf_status hgf_aggregate_plain(hgf_ctx *ctx, const hgf_guidance *g, const void *cost,
                                int cost_dtype, int L, void *filtered, int filtered_dtype,
                                int32_t *labels, float *best, void *stream) {
+  NvtxRange nvtx_range("hgf_aggregate_plain");
   hgf_status st = enter(ctx);
   if (st != HGF_OK) return st;
   st = check_outputs(ctx, g, cost, cost_dtype, L, filtered, filtered_dtype, labels, best);
@@ -468,6 +475,7 @@ hgf_status hgf_aggregate_plain(hgf_ctx *ctx, const hgf_guidance *g, const void *
 
 hgf_status hgf_wta(hgf_ctx *ctx, const void *filtered, int dtype, int L, int H, int W,
                    int32_t *labels, float *best, void *stream) {
+  NvtxRange nvtx_range("hgf_wta");
   hgf_status st = enter(ctx);
   if (st != HGF_OK) return st;
   if (!filtered || (!labels && !best)) return set_err(ctx, HGF_EINVAL, "NULL argument");
@@ -483,6 +491,7 @@ hgf_status hgf_wta(hgf_ctx *ctx, const void *filtered, int dtype, int L, int H, 
 hgf_status hgf_filter_host(hgf_ctx *ctx, const float *img, int C, int H, int W,
                            const hgf_params *params, const void *cost, int cost_dtype, int L,
                            int32_t *labels, float *best, void *stream) {
+  NvtxRange nvtx_range("hgf_filter_host");
   hgf_status st = enter(ctx);
   if (st != HGF_OK) return st;
   if (!img || !cost || (!labels && !best)) return set_err(ctx, HGF_EINVAL, "NULL argument");
@@ -504,10 +513,22 @@ hgf_status hgf_filter_host(hgf_ctx *ctx, const float *img, int C, int H, int W,
   void *cost_d = base + img_b;
   int32_t *labels_d = (int32_t *)(base + img_b + cost_b);
   float *best_d = (float *)(base + img_b + cost_b + out_b);
-  cudaError_t e = cudaMemcpyAsync(img_d, img, (size_t)C * HW * 4, cudaMemcpyHostToDevice, s);
+  // the cost volume (the bulk of the upload) goes over a second stream, concurrently with the
+  // image upload and the guidance precompute; the aggregation waits for it
+  cudaError_t e = cudaSuccess;
+  if (!ctx->io_stream) e = cudaStreamCreateWithFlags(&ctx->io_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !ctx->io_fork)
+    e = cudaEventCreateWithFlags(&ctx->io_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess && !ctx->io_done)
+    e = cudaEventCreateWithFlags(&ctx->io_done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->io_fork, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->io_stream, ctx->io_fork, 0);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(cost_d, cost, (size_t)L * HW * dtype_size(cost_dtype),
-                        cudaMemcpyHostToDevice, s);
+                        cudaMemcpyHostToDevice, ctx->io_stream);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->io_done, ctx->io_stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(img_d, img, (size_t)C * HW * 4, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail_locked(ctx, e, "hgf_filter_host upload");
   if (!same_shape(ctx->host_guidance, C, H, W, params)) {
     if (ctx->host_guidance) {
@@ -523,6 +544,8 @@ hgf_status hgf_filter_host(hgf_ctx *ctx, const float *img, int C, int H, int W,
   }
   st = prepare_locked(ctx, ctx->host_guidance, img_d, s);
   if (st != HGF_OK) return st;
+  e = cudaStreamWaitEvent(s, ctx->io_done, 0);
+  if (e != cudaSuccess) return cuda_fail_locked(ctx, e, "hgf_filter_host upload wait");
   st = aggregate_locked(ctx, ctx->host_guidance, cost_d, cost_dtype, L, nullptr,
                         labels ? labels_d : nullptr, best ? best_d : nullptr, s);
   if (st != HGF_OK) return st;
@@ -540,6 +563,7 @@ hgf_status hgf_filter_host(hgf_ctx *ctx, const float *img, int C, int H, int W,
 hgf_status hgf_aggregate_stereo(hgf_ctx *ctx, const hgf_guidance *g, const float *other, int L,
                                 const hgf_cost_params *p, void *filtered, int filtered_dtype,
                                 int32_t *labels, float *best, void *stream) {
+  NvtxRange nvtx_range("hgf_aggregate_stereo");
   hgf_status st = enter(ctx);
   if (st != HGF_OK) return st;
   if (!other || !p) return set_err(ctx, HGF_EINVAL, "NULL argument");
@@ -579,6 +603,7 @@ hgf_status hgf_aggregate_stereo(hgf_ctx *ctx, const hgf_guidance *g, const float
 
 hgf_status hgf_refine_lr(hgf_ctx *ctx, const int32_t *disp_left, const int32_t *disp_right, int H,
                          int W, int threshold, int32_t *out, uint8_t *keep, void *stream) {
+  NvtxRange nvtx_range("hgf_refine_lr");
   hgf_status st = enter(ctx);
   if (st != HGF_OK) return st;
   if (!disp_left || !disp_right || !out || !keep) return set_err(ctx, HGF_EINVAL, "NULL argument");
@@ -595,6 +620,7 @@ hgf_status hgf_refine_lr(hgf_ctx *ctx, const int32_t *disp_left, const int32_t *
 
 hgf_status hgf_cost_volume(hgf_ctx *ctx, const float *ref, const float *other, int C, int H, int W,
                            int L, const hgf_cost_params *p, int dtype, void *out, void *stream) {
+  NvtxRange nvtx_range("hgf_cost_volume");
   hgf_status st = enter(ctx);
   if (st != HGF_OK) return st;
   if (!ref || !other || !p || !out) return set_err(ctx, HGF_EINVAL, "NULL argument");
@@ -616,6 +642,7 @@ hgf_status hgf_cost_volume(hgf_ctx *ctx, const float *ref, const float *other, i
 
 hgf_status hgf_batched_inverse(hgf_ctx *ctx, const double *S, int count, int n, double lambda,
                                int method, int precision, double *out, void *stream) {
+  NvtxRange nvtx_range("hgf_batched_inverse");
   hgf_status st = enter(ctx);
   if (st != HGF_OK) return st;
   if (!S || !out) return set_err(ctx, HGF_EINVAL, "NULL argument");
@@ -646,6 +673,7 @@ hgf_status hgf_device_status(hgf_ctx *ctx, int *status, int clear) {
 
 
 hgf_status hgf_guidance_update(hgf_ctx *ctx, hgf_guidance *g, const float *img, void *stream) {
+  NvtxRange nvtx_range("hgf_guidance_update");
   hgf_status st = enter(ctx);
   if (st != HGF_OK) return st;
   if (!g || g->ctx != ctx) return set_err(ctx, HGF_EINVAL, "bad guidance handle");

@@ -11,6 +11,7 @@
 #include <string>
 #include <type_traits>
 #include <vector>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/hgf.h"
 
@@ -122,6 +123,14 @@ struct Workspace {
 
 // Per-context kernel instrumentation: a launch counter (always on) and, when enabled, a CUDA
 // event pair recorded on the launching stream around every kernel launch.
+// NVTX range around an API call (visible in Nsight Systems timelines; a no-op without a tool).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 struct Profiler {
   bool enabled = false;
   unsigned long long launches = 0;
@@ -183,6 +192,9 @@ struct hgf_ctx {
   hgf::Workspace ws_plain;       // plain-form intermediates
   hgf::Workspace ws_io;          // device copies for hgf_filter_host
   hgf::Workspace ws_grad;        // gradient planes of hgf_aggregate_stereo
+  // hgf_filter_host uploads the cost volume on io_stream while the guidance precompute runs
+  cudaStream_t io_stream = nullptr;
+  cudaEvent_t io_fork = nullptr, io_done = nullptr;
   hgf_guidance *host_guidance = nullptr;  // reused by hgf_filter_host
   hgf_tuning tuning{0, 0, 0, 0};
   int num_sms = 0;

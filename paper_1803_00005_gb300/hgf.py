@@ -418,6 +418,34 @@ def hgf_autotune(ctx, g, cost, labels, reps=3, stream=None):
                 chunk_labels=t.chunk_labels, apply_mode=t.apply_mode), n.value
 
 
+def autotune_cached(ctx, g, cost, labels, cache_path, reps=3, stream=None):
+    """hgf_autotune behind a JSON cache file keyed by GPU name, guidance channels n, radius r,
+    cost dtype and size class (H*W and L rounded up to powers of two). A hit sets the cached
+    tuning on ctx without timing anything. Returns (tuning dict, hit)."""
+    import json
+    import os
+    import torch
+    info = hgf_guidance_info(g)
+    pow2 = lambda v: 1 << max(0, int(v - 1).bit_length())  # noqa: E731
+    key = "|".join(str(x) for x in (torch.cuda.get_device_name(cost.device), info["n"],
+                                     info["r"], str(cost.dtype).replace("torch.", ""),
+                                     pow2(info["H"] * info["W"]), pow2(cost.shape[0])))
+    cache = {}
+    if os.path.exists(cache_path):
+        with open(cache_path) as f:
+            cache = json.load(f)
+    if key in cache:
+        hgf_set_tuning(ctx, **cache[key])
+        return dict(cache[key]), True
+    tuning, _ = hgf_autotune(ctx, g, cost, labels, reps=reps, stream=stream)
+    cache[key] = tuning
+    tmp = cache_path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, cache_path)
+    return tuning, False
+
+
 def hgf_device_status(ctx, clear=False):
     """Watchdog word of ctx's device after all its work: 0 unless a bounded wait in a kernel ran
     out (that call's results are then incomplete)."""

@@ -44,3 +44,25 @@ def test_autotune_preserves_results():
         hgf.hgf_guidance_release(g)
     finally:
         hgf.hgf_destroy(ctx)
+
+
+def test_autotune_cache_roundtrip(tmp_path):
+    """autotune_cached: the first call times and stores the tuning under its key, the second is a
+    hit that sets the same tuning without timing."""
+    torch = torch_cuda()
+    from paper_1803_00005_gb300 import build, hgf
+    build.build()
+    case = synth.make_case(160, 120, 20, 39, "f32")
+    ctx = hgf.hgf_create(0)
+    try:
+        img = torch.from_numpy(case.guidance).cuda()
+        cost = torch.from_numpy(case.cost).cuda()
+        g = hgf.hgf_prepare(ctx, img, hgf.make_params(degree=1, r=4, eps=1e-4))
+        lab = torch.empty((120, 160), dtype=torch.int32, device="cuda")
+        path = str(tmp_path / "tune.json")
+        t1, hit1 = hgf.autotune_cached(ctx, g, cost, lab, path, reps=1)
+        t2, hit2 = hgf.autotune_cached(ctx, g, cost, lab, path, reps=1)
+        assert (hit1, hit2) == (False, True) and t1 == t2
+        hgf.hgf_guidance_release(g)
+    finally:
+        hgf.hgf_destroy(ctx)
