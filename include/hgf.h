@@ -105,6 +105,8 @@ hgf_status hgf_make_guidance(hgf_ctx *ctx, const float *img, int C, int H, int W
 /* Guidance precompute (Sec. 5.3: guidance-only box filtering is done once per guidance):
  * polynomial guidance G, means mu = A(G), covariance Sigma = A(G G^T) - mu mu^T plus eps E
  * (Sec. 5.1) and its inverse by Prop. 1 (Sec. 3), kept resident in a handle the library owns.
+ * With params->form = HGF_FORM_PAPER, the (n+1) x (n+1) inverse of lambda E + Gram (window sums,
+ * G_0 = 1) instead.
  * img: device, C x H x W float32, may be freed once the call's work has completed (the handle
  * keeps a copy). The handle's memory is allocated here (HGF_ENOMEM on failure) and freed by
  * hgf_guidance_release. Bounds: C in {1,3}, 1 <= n <= 19, H, W >= 1, r >= 0, eps > 0. */
@@ -128,7 +130,9 @@ hgf_status hgf_guidance_export(hgf_ctx *ctx, const hgf_guidance *g, float *minv_
 /* Fused aggregation + WTA (Sec. 1 pipeline; Eqs. GF_w / HGF_z1): for every label slice p of the
  * cost volume, pbar = A(p), cov_i = A(G_i p) - mu_i pbar, a = (Sigma + eps E)^-1 cov,
  * b = pbar - a.mu, q = sum_i A(a_i) G_i + A(b); then labels = argmin_l q_l (lowest l on ties,
- * NaN counted as +inf) and best = min_l q_l.
+ * NaN counted as +inf) and best = min_l q_l. For a guidance prepared with HGF_FORM_PAPER the
+ * coefficients are those of the paper's form instead: w = (lambda E + Gram)^-1 B([1, G] p) and
+ * q = sum_i A(w_i) G_i + A(w_0) (see hgf_form).
  * cost: device, L x H x W of cost_dtype (HGF_F32, HGF_BF16 or HGF_F16), H, W of the guidance.
  * filtered: device L x H x W of filtered_dtype (HGF_F32) or NULL; labels: device int32 H x W or
  * NULL; best: device float32 H x W or NULL. At least one output must be non-NULL.

@@ -405,9 +405,11 @@ __device__ __forceinline__ void store_record(float *rec, const float *out, int x
   }
 }
 
-// Centred form, one thread per pixel. Dividing the window sums of the (shifted) moments by N
-// gives the means mu_i = A(G_i) and E_ij = A(G_i G_j); S = E - mu mu^T (Sec. 5.1), Prop. 1 with
-// lambda = eps. Record: [mu | packed (S + eps E)^-1 | 0].
+// Centred form, one thread per pixel, in window-sum units: with the window sums s_i = B(G_i) and
+// s_ij = B(G_i G_j) of the (shifted) guidance, N Sigma = T with T_ij = s_ij - (s_i / N) s_j, and
+// (Sigma + eps E)^-1 = N (N eps E + T)^-1. Prop. 1 runs on T with lambda' = N eps (Sec. 3; Sec. 5.1
+// for the centred moments), which saves the per-entry division by N; the record then holds
+// [mu | packed N (lambda' E + T)^-1 | 0] with mu = s / N.
 template <int NG, typename T>
 __global__ void __launch_bounds__(128) k_inverse(const float *__restrict__ mom, int H, int W,
                                                  int r, double eps, int combine,
@@ -420,25 +422,30 @@ __global__ void __launch_bounds__(128) k_inverse(const float *__restrict__ mom, 
   if (x >= W) return;
   size_t HW = (size_t)H * W;
   size_t pix = (size_t)y * W + x;
-  const T invN = T(1) / T(clipped_count(x, r, W) * clipped_count(y, r, H));
+  const int Ni = clipped_count(x, r, W) * clipped_count(y, r, H);
+  const T Nn = T(Ni);
+  const T invN = T(1) / Nn;
 
   float raw[NG + P];
 #pragma unroll
   for (int e = 0; e < NG + P; ++e) raw[e] = __ldg(mom + (size_t)e * HW + pix);
-  T m[NG];
+  T m[NG], sd[NG];
 #pragma unroll
-  for (int i = 0; i < NG; ++i) m[i] = T(raw[i]) * invN;
-  T S[P];
+  for (int i = 0; i < NG; ++i) {
+    sd[i] = T(raw[i]);
+    m[i] = sd[i] * invN;
+  }
+  T S[P];  // N x covariance
 #pragma unroll
   for (int i = 0; i < NG; ++i) {
 #pragma unroll
     for (int j = i; j < NG; ++j) {
       const int e = tri_index(NG, i, j);
-      S[e] = T(raw[NG + e]) * invN - m[i] * m[j];
+      S[e] = fma(-m[i], sd[j], T(raw[NG + e]));
     }
   }
 
-  const T lam = T(eps);
+  const T lam = T(eps) * Nn;
   const T inv_lam = T(1) / lam;
   T al[P];
   prop1_alpha<NG, T>(S, inv_lam, al);
@@ -447,12 +454,20 @@ __global__ void __launch_bounds__(128) k_inverse(const float *__restrict__ mom, 
   float out[REC];
 #pragma unroll
   for (int i = 0; i < NG; ++i) out[i] = (float)m[i];
+  if (combine == HGF_COMBINE_W3) {
+    const float nf = (float)Ni;  // exact
 #pragma unroll
-  for (int i = 0; i < NG; ++i)
+    for (int i = 0; i < NG; ++i)
 #pragma unroll
-    for (int j = i; j < NG; ++j)
-      out[NG + tri_index(NG, i, j)] =
-          (float)inverse_entry<NG, T>(S, al, lam, inv_lam, combine, i, j);
+      for (int j = i; j < NG; ++j)
+        out[NG + tri_index(NG, i, j)] =
+            (float)inverse_entry<NG, T>(S, al, lam, inv_lam, combine, i, j) * nf;
+  } else {
+    // N (lambda' E + T)^-1 = -N lambda' alpha: one float64 product, then float32 scaling
+    const float f = (float)(-(lam * Nn));
+#pragma unroll
+    for (int e = 0; e < P; ++e) out[NG + e] = (float)al[e] * f;
+  }
 #pragma unroll
   for (int e = NG + P; e < REC; ++e) out[e] = 0.f;
 #pragma unroll

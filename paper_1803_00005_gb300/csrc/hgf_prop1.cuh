@@ -13,6 +13,21 @@ namespace hgf {
 //   alpha_ij += gamma u_i u_j (i, j < kappa);  alpha_{i kappa} = gamma u_i / lambda;
 //   alpha_{kappa kappa} = gamma / lambda^2
 // which yields (lambda E + S)^-1 = lambda^-1 E + S alpha (Eq. HGF_w3) = -lambda alpha.
+// -1 / d. For float64, the Newton-Raphson iteration for the reciprocal, r <- r + r (1 - d r), from
+// the float32 reciprocal of d: each step doubles the correct bits (24 -> 48 -> 53), two steps
+// give the float64 result to within an ulp with four fused multiply-adds. d > 0 here (the
+// recursion's denominators are >= 1 for positive semidefinite S), and |d| stays far inside the
+// float32 range.
+template <typename T>
+__device__ __forceinline__ T neg_recip(T d) { return T(-1) / d; }
+template <>
+__device__ __forceinline__ double neg_recip<double>(double d) {
+  double r = (double)__frcp_rn((float)d);
+  r = fma(r, fma(-d, r, 1.0), r);
+  r = fma(r, fma(-d, r, 1.0), r);
+  return -r;
+}
+
 template <int M, typename T>
 __device__ __forceinline__ void prop1_alpha(const T *S, T inv_lam, T *al) {
 #pragma unroll
@@ -31,7 +46,7 @@ __device__ __forceinline__ void prop1_alpha(const T *S, T inv_lam, T *al) {
     T den = T(1) + S[tri_index(M, k, k)] * inv_lam;
 #pragma unroll
     for (int i = 0; i < k; ++i) den = fma(S[tri_index(M, i, k)], u[i], den);
-    const T gam = T(-1) / den;
+    const T gam = neg_recip(den);
 #pragma unroll
     for (int i = 0; i < k; ++i) {
       const T v = gam * u[i];
