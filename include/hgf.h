@@ -364,6 +364,11 @@ hgf_status hgf_launch_count(hgf_ctx *ctx, unsigned long long *out);
  * ctx's device, writes the word to *status (0: no wait ran out) and, when clear is nonzero,
  * resets it. hgf_filter_host checks it itself and returns HGF_ETIMEOUT when it is set. */
 hgf_status hgf_device_status(hgf_ctx *ctx, int *status, int clear);
+/* Watchdog test hook (no counterpart in the paper): enqueues one CTA that waits, bounded, on an
+ * mbarrier nothing arrives on - the same wait k_coef uses for its record copies - so that the
+ * wait runs out after limit_us microseconds (1 .. 10^7), sets the device status word and returns.
+ * Nothing faults, traps or spins unbounded; the context stays usable. HGF_EINVAL on a bad limit. */
+hgf_status hgf_watchdog_probe(hgf_ctx *ctx, int limit_us, void *stream);
 hgf_status hgf_profile_enable(hgf_ctx *ctx, int enable);
 hgf_status hgf_profile_report(hgf_ctx *ctx, char *buf, size_t cap);
 

@@ -2,6 +2,7 @@
 // pass, bands, chunks), dispatch to the per-basis kernels of hgf_fused.cuh (compiled in the
 // hgf_fused_*.cu translation units), the kernel watchdog word, and the WTA kernels.
 #include "hgf_basis.cuh"
+#include "hgf_mbarrier.cuh"
 
 #include <algorithm>
 #include <mutex>
@@ -40,6 +41,20 @@ __global__ void k_wta_volume(const float *__restrict__ q, int L, int HW,
   }
   if (labels) labels[p] = lb;
   if (best) best[p] = b;
+}
+
+// Watchdog probe: one CTA waits, bounded, on an mbarrier that nothing arrives on (it expects one
+// arrival that never comes), exactly as k_coef waits for a record copy; when the limit runs out
+// it records the timeout in the status word and returns. No copy is in flight, so the CTA exits
+// cleanly.
+__global__ void k_watchdog_probe(int *status, unsigned long long limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(&bar, 0, limit_ns)) atomicExch(status, 1);
 }
 
 }  // namespace
@@ -88,6 +103,13 @@ cudaError_t read_device_status(int *status, bool clear) {
   }
   *status = v;
   return e;
+}
+
+cudaError_t launch_watchdog_probe(unsigned long long limit_ns, cudaStream_t s) {
+  int *status = device_status_ptr();
+  if (!status) return cudaErrorInvalidValue;
+  k_watchdog_probe<<<1, 32, 0, s>>>(status, limit_ns);
+  return cudaGetLastError();
 }
 
 bool aggregate_fits(const hgf_guidance *g) {

@@ -660,6 +660,18 @@ hgf_status hgf_batched_inverse(hgf_ctx *ctx, const double *S, int count, int n, 
   return HGF_OK;
 }
 
+hgf_status hgf_watchdog_probe(hgf_ctx *ctx, int limit_us, void *stream) {
+  hgf_status st = enter(ctx);
+  if (st != HGF_OK) return st;
+  if (limit_us < 1 || limit_us > 10000000)
+    return set_err(ctx, HGF_EINVAL, "limit_us must be in 1 .. 10^7");
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  cudaError_t e = launch_watchdog_probe((unsigned long long)limit_us * 1000ull,
+                                        (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail_locked(ctx, e, "hgf_watchdog_probe");
+  return HGF_OK;
+}
+
 hgf_status hgf_device_status(hgf_ctx *ctx, int *status, int clear) {
   hgf_status st = enter(ctx);
   if (st != HGF_OK) return st;

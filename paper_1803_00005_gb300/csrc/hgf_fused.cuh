@@ -22,6 +22,7 @@
 #include "hgf_basis.cuh"
 #include "hgf_stereo.cuh"
 #include "hgf_scan.cuh"
+#include "hgf_mbarrier.cuh"
 
 #include <algorithm>
 #include <type_traits>
@@ -37,42 +38,8 @@ using strip::kRowStride;
 using strip::scan_rows;
 using strip::window;
 
-// ---- bulk asynchronous copies of inverse records into shared memory (mbarrier completion)
-constexpr int kWaitLimit = 1 << 22;  // try_wait polls before a wait gives up (seconds, not cycles)
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-// Thread that issues: expect `bytes` on `bar` and copy them from global `src` to shared `dst`.
-__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes,
-                                              uint64_t *bar) {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-// Bounded wait for phase `parity` of `bar`; false if the limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-  for (int it = 0; it < kWaitLimit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
+// bulk asynchronous copies and bounded mbarrier waits: hgf_mbarrier.cuh
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // a bounded wait gives up after 1 s
 
 // Strip-tiled inverse records (n <= 9) are staged in shared memory, a double buffer filled one
 // row ahead by bulk copies; pixel-major ones (n = 19) are loaded by phase C itself.
@@ -294,12 +261,12 @@ __global__ void __launch_bounds__(NT, (coef_min_blocks<B, K, COMP>())) k_coef(co
       if (kRecordBuffers == 1 && y1 > Y0) issue_records(y1);
     }
     scan_rows<(K * C1 + NT / 32 - 1) / (NT / 32)>(sA, nk * C1);
-    if (STAGE && !mbar_wait(&bars[rbuf(y1)], rpar(y1))) s_fail = 1;
+    if (STAGE && !mbar_wait(&bars[rbuf(y1)], rpar(y1), kWaitLimitNs)) s_fail = 1;
     __syncthreads();
     if (STAGE && s_fail) {  // a copy never completed: report, drain with a bound, stop
       if (t == 0) {
         atomicExch(status, 1);
-        if (kRecordBuffers == 2 && y1 + 1 < Y1) mbar_wait(&bars[rbuf(y1 + 1)], rpar(y1 + 1));
+        if (kRecordBuffers == 2 && y1 + 1 < Y1) mbar_wait(&bars[rbuf(y1 + 1)], rpar(y1 + 1), kWaitLimitNs);
       }
       failed = true;
       return;

@@ -277,6 +277,8 @@ cudaError_t launch_batched_inverse(const double *S, int count, int n, double lam
 size_t coef_smem(int n, int C, int K, int r);
 // Device address of the current device's watchdog word (hgf_device_status).
 int *device_status_ptr();
+// One CTA whose bounded wait cannot complete: it times out after limit_ns and sets the word.
+cudaError_t launch_watchdog_probe(unsigned long long limit_ns, cudaStream_t s);
 template <int B>
 cudaError_t launch_basis(const hgf_guidance *g, const void *cost, int cost_dtype, int L,
                          float *filtered, float *coef_ws, unsigned long long *keys,

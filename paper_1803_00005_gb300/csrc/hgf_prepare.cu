@@ -83,12 +83,14 @@ template <int B>
 __global__ void __launch_bounds__(kMeanThreads) k_mean_partial(const float *__restrict__ img,
                                                                int HW,
                                                                double *__restrict__ partial) {
+  // the shift only conditions the float32 sums (the centred form is exactly invariant to it), so
+  // float32 sums of a few pixels per thread are plenty; the block totals are kept in float64
   constexpr int N = basis_n(B), C = basis_channels_in(B);
-  __shared__ double red[kMeanThreads / 32][N];
+  __shared__ float red[kMeanThreads / 32][N];
   const float zero[N] = {};
-  double acc[N];
+  float acc[N];
 #pragma unroll
-  for (int i = 0; i < N; ++i) acc[i] = 0.0;
+  for (int i = 0; i < N; ++i) acc[i] = 0.f;
   const int per = (HW + gridDim.x - 1) / gridDim.x;
   const int p0 = blockIdx.x * per, p1 = min(HW, p0 + per);
   for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
@@ -102,7 +104,7 @@ __global__ void __launch_bounds__(kMeanThreads) k_mean_partial(const float *__re
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    double v = acc[i];
+    float v = acc[i];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
     if (lane == 0) red[warp][i] = v;
@@ -110,39 +112,48 @@ __global__ void __launch_bounds__(kMeanThreads) k_mean_partial(const float *__re
   __syncthreads();
   if (threadIdx.x < N) {
     double s = 0.0;
-    for (int w = 0; w < kMeanThreads / 32; ++w) s += red[w][threadIdx.x];
+    for (int w = 0; w < kMeanThreads / 32; ++w) s += (double)red[w][threadIdx.x];
     partial[blockIdx.x * N + threadIdx.x] = s;
   }
 }
 
-// One warp per channel: lane l sums partials l, l + 32, ..., then a fixed shuffle tree (the
-// order is fixed, so every call gives the same shift).
-__global__ void k_mean_final(const double *__restrict__ partial, int nblk, int n, int HW,
-                             float *__restrict__ shift) {
-  const int i = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (i >= n) return;
-  double s = 0.0;
-  for (int b = lane; b < nblk; b += 32) s += partial[b * n + i];
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-  if (lane == 0) shift[i] = (float)(s / HW);
-}
-
-// Shifted guidance planes G_i - c_i (used by the moment sums and the plain form).
+// Shifted guidance planes G_i - c_i (used by the moment sums and the plain form). Every CTA
+// first reduces the per-block partial sums to the image means c_i itself (one warp per channel,
+// a fixed order, so all CTAs get identical values); CTA 0 also stores them in `shift`.
 template <int B>
-__global__ void k_shifted_guidance(const float *__restrict__ img, const float *__restrict__ shift,
-                                   int HW, float *__restrict__ G) {
+__global__ void __launch_bounds__(256) k_shifted_guidance(const float *__restrict__ img,
+                                                          const double *__restrict__ partial,
+                                                          int nblk, int HW,
+                                                          float *__restrict__ shift,
+                                                          float *__restrict__ G) {
   constexpr int N = basis_n(B), C = basis_channels_in(B);
-  const size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (p >= (size_t)HW) return;
-  float x[C], sh[N], g[N];
+  __shared__ float sh_s[N];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int i = warp; i < N; i += nwarp) {
+    double s = 0.0;
+    for (int b = lane; b < nblk; b += 32) s += partial[b * N + i];
 #pragma unroll
-  for (int c = 0; c < C; ++c) x[c] = img[(size_t)c * HW + p];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) {
+      const float c = (float)(s / HW);
+      sh_s[i] = c;
+      if (blockIdx.x == 0) shift[i] = c;
+    }
+  }
+  __syncthreads();
+  float sh[N];
 #pragma unroll
-  for (int i = 0; i < N; ++i) sh[i] = shift[i];
-  eval_basis<B>(x, sh, g);
+  for (int i = 0; i < N; ++i) sh[i] = sh_s[i];
+  // grid-stride over pixels: a few pixels per thread, so that fewer CTAs repeat the reduction
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < (size_t)HW;
+       p += (size_t)gridDim.x * blockDim.x) {
+    float x[C], g[N];
 #pragma unroll
-  for (int i = 0; i < N; ++i) G[(size_t)i * HW + p] = g[i];
+    for (int c = 0; c < C; ++c) x[c] = img[(size_t)c * HW + p];
+    eval_basis<B>(x, sh, g);
+#pragma unroll
+    for (int i = 0; i < N; ++i) G[(size_t)i * HW + p] = g[i];
+  }
 }
 
 // ------------------------------------------------------------------ moment window sums (strips)
@@ -613,12 +624,9 @@ cudaError_t launch_prepare(hgf_guidance *g, const float *img, void *ws, size_t w
       k_mean_partial<B><<<kMeanBlocks, kMeanThreads, 0, s>>>(g->img, HW, partial);
     }
     {
-      LaunchScope ls(prof, "k_mean_final", s);
-      k_mean_final<<<1, 32 * n, 0, s>>>(partial, kMeanBlocks, n, HW, g->shift);
-    }
-    {
       LaunchScope ls(prof, "k_shifted_guidance", s);
-      k_shifted_guidance<B><<<(HW + 255) / 256, 256, 0, s>>>(g->img, g->shift, HW, g->G);
+      k_shifted_guidance<B><<<(HW + 1023) / 1024, 256, 0, s>>>(g->img, partial, kMeanBlocks, HW,
+                                                               g->shift, g->G);
     }
   });
   if (n <= 9 && 2 * g->r + 1 < kStripThreads) {

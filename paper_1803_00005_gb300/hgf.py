@@ -38,7 +38,7 @@ EXPORTED = [
     "hgf_serve_wait", "hgf_serve_stats", "hgf_serve_inject_alloc_failures", "hgf_serve_destroy",
     "hgf_batch_create", "hgf_batch_run", "hgf_batch_launch_graph", "hgf_batch_destroy",
     "hgf_device_status", "hgf_batched_inverse", "hgf_cost_volume", "hgf_aggregate_stereo",
-    "hgf_refine_lr", "hgf_autotune",
+    "hgf_refine_lr", "hgf_autotune", "hgf_watchdog_probe",
 ]
 
 
@@ -139,6 +139,7 @@ def lib():
         "hgf_guidance_update": (c_int, [vp, vp, vp, vp]),
         "hgf_launch_count": (c_int, [vp, P(ctypes.c_ulonglong)]),
         "hgf_device_status": (c_int, [vp, P(c_int), c_int]),
+        "hgf_watchdog_probe": (c_int, [vp, c_int, vp]),
         "hgf_batched_inverse": (c_int, [vp, vp, c_int, c_int, c_double, c_int, c_int, vp, vp]),
         "hgf_cost_volume": (c_int, [vp, vp, vp, c_int, c_int, c_int, c_int, P(hgf_cost_params),
                                     c_int, vp, vp]),
@@ -444,6 +445,12 @@ def autotune_cached(ctx, g, cost, labels, cache_path, reps=3, stream=None):
         json.dump(cache, f, indent=1, sort_keys=True)
     os.replace(tmp, cache_path)
     return tuning, False
+
+
+def hgf_watchdog_probe(ctx, limit_us, stream=None):
+    """Enqueues a wait that nothing completes; it times out after limit_us and sets the device
+    status word (test hook for the kernels' bounded waits)."""
+    _check(ctx, lib().hgf_watchdog_probe(ctx, int(limit_us), _stream(stream)))
 
 
 def hgf_device_status(ctx, clear=False):
