@@ -684,38 +684,41 @@ def main():
                                           pin_cost.element_size()),
                    d2h_bytes_per_step=int(H * W * 4))
 
-    # end to end from the stereo pair itself: both views uploaded from pinned host memory, the
-    # cost computed inside the coefficient kernel (hgf_aggregate_stereo), labels read back
-    e2e_stereo = None
+    # end to end from the stereo pair itself through hgf_stereo_host: both views uploaded from
+    # pinned host memory, the cost computed inside the coefficient kernel, labels read back;
+    # `stereo_pipeline` adds the right view's aggregation and the left-right refinement
+    e2e_stereo = stereo_pipeline = None
     if not args.no_e2e and args.impl == "fused":
         left, right, _ = synth.stereo_pair(W, H, L, w["seed"])
         pin_l = torch.from_numpy(left.astype(np.float32)).pin_memory()
         pin_r = torch.from_numpy(right.astype(np.float32)).pin_memory()
-        pin_lab = torch.empty((H, W), dtype=torch.int32).pin_memory()
-        dl = torch.empty_like(pin_l, device=dev)
-        dr = torch.empty_like(pin_r, device=dev)
+        pin_d = torch.empty((H, W), dtype=torch.int32).pin_memory()
+        sctx = hgf.hgf_create(local_rank)
 
-        def stereo_step():
-            dl.copy_(pin_l, non_blocking=True)
-            dr.copy_(pin_r, non_blocking=True)
-            hgf.hgf_guidance_update(ctx, g, dl)
-            hgf.hgf_aggregate_stereo(ctx, g, dr, L, labels=labels)
-            pin_lab.copy_(labels, non_blocking=True)
-            torch.cuda.current_stream().synchronize()
+        def run_pipeline(refine, steps):
+            for _ in range(3):
+                hgf.hgf_stereo_host(sctx, pin_l.numpy(), pin_r.numpy(), L, params, refine=refine,
+                                    out=pin_d.numpy())
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                hgf.hgf_stereo_host(sctx, pin_l.numpy(), pin_r.numpy(), L, params, refine=refine,
+                                    out=pin_d.numpy())
+            ts = time.perf_counter() - t0
+            return world_max(ts, dist, dev) if world > 1 else ts
 
-        for _ in range(3):
-            stereo_step()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            stereo_step()
-        ts = time.perf_counter() - t0
-        if world > 1:
-            ts = world_max(ts, dist, dev)
+        ts = run_pipeline(False, args.steps)
         e2e_stereo = dict(value=whole_job_value(units, world, ts), unit=UNIT,
                           h2d_bytes_per_step=int(2 * pin_l.numel() * 4),
                           d2h_bytes_per_step=int(H * W * 4),
-                          note="stereo pair in, labels out; cost computed on the device "
-                               "(truncated colour + gradient, inside the coefficient kernel)")
+                          note="hgf_stereo_host: stereo pair in, disparity out; cost computed "
+                               "on the device inside the coefficient kernel")
+        nref = max(3, args.steps // 4)
+        tr = run_pipeline(True, nref)
+        stereo_pipeline = dict(ms_per_frame=1e3 * tr / nref,
+                               note="hgf_stereo_host with refinement: cost, aggregation and WTA "
+                                    "for both views, left-right check, hole filling; from host "
+                                    "views to host disparity")
+        hgf.hgf_destroy(sctx)
 
     hgf.hgf_guidance_release(g)
     hgf.hgf_destroy(ctx)
@@ -730,6 +733,7 @@ def main():
                                 step="guidance precompute + aggregate + WTA"),
                     roofline=roof, hbm=hbm, cpu_baseline=cpu,
                     cpu_baseline_all_cores=cpu_all, e2e=e2e, e2e_stereo=e2e_stereo,
+                    stereo_pipeline=stereo_pipeline,
                     gpu_launches=int(launches),
                     clocks=clk, kernels=kernels, wall_s=wall,
                     step_ms=dict(min=min(step_ms), median=statistics.median(step_ms)))

@@ -320,6 +320,20 @@ hgf_status hgf_aggregate_stereo(hgf_ctx *ctx, const hgf_guidance *g, const float
                                 const hgf_cost_params *p, void *filtered, int filtered_dtype,
                                 int32_t *labels, float *best, void *stream);
 
+/* The stereo pipeline of the cost-volume filtering framework (Sec. 6: cost computation,
+ * aggregation, WTA, post processing) in one call from host memory: uploads the left and right
+ * views (host float32 C x H x W; the right one on a library stream while the left guidance is
+ * prepared), prepares the left view's guidance, aggregates the cost of hgf_cost_volume for
+ * disparities 0..L-1 with WTA computing the cost on the fly (hgf_aggregate_stereo, direction +1;
+ * cost->direction is ignored), and with refine = 1 also the right view's (direction -1) followed
+ * by hgf_refine_lr(threshold). Writes the disparity map to `disparity` (host int32 H x W) and
+ * returns once it is there. Guidance handles and workspace are kept in ctx between calls (no
+ * allocation when shapes repeat). Errors as hgf_prepare, hgf_aggregate_stereo and hgf_refine_lr;
+ * HGF_EINVAL for refine not 0 or 1; HGF_ETIMEOUT if a bounded wait in a kernel ran out. */
+hgf_status hgf_stereo_host(hgf_ctx *ctx, const float *left, const float *right, int C, int H,
+                           int W, int L, const hgf_params *params, const hgf_cost_params *cost,
+                           int refine, int threshold, int32_t *disparity, void *stream);
+
 /* ---------------------------------------------------------------------------------------------
  * Post-WTA refinement of a stereo disparity map: the post-processing step that follows WTA in
  * the cost-volume filtering framework of the stereo experiment (Sec. 6). The paper only names the

@@ -271,6 +271,10 @@ hgf_status hgf_destroy(hgf_ctx *ctx) {
   if (!ctx) return HGF_OK;
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
+  if (ctx->host_guidance_right) {
+    cudaFree(ctx->host_guidance_right->rec);
+    delete ctx->host_guidance_right;
+  }
   if (ctx->host_guidance) {
     cudaFree(ctx->host_guidance->rec);
     delete ctx->host_guidance;
@@ -560,27 +564,25 @@ hgf_status hgf_filter_host(hgf_ctx *ctx, const float *img, int C, int H, int W,
   return HGF_OK;
 }
 
-hgf_status hgf_aggregate_stereo(hgf_ctx *ctx, const hgf_guidance *g, const float *other, int L,
-                                const hgf_cost_params *p, void *filtered, int filtered_dtype,
-                                int32_t *labels, float *best, void *stream) {
-  NvtxRange nvtx_range("hgf_aggregate_stereo");
-  hgf_status st = enter(ctx);
-  if (st != HGF_OK) return st;
-  if (!other || !p) return set_err(ctx, HGF_EINVAL, "NULL argument");
-  // the cost is made here, not read: check the outputs with a stand-in cost pointer
-  st = check_outputs(ctx, g, other, HGF_F32, L, filtered, filtered_dtype, labels, best);
-  if (st != HGF_OK) return st;
+namespace {
+
+hgf_status check_cost_params(hgf_ctx *ctx, const hgf_cost_params *p) {
   if (!(p->alpha >= 0.0 && p->alpha <= 1.0) || !(p->tau_color >= 0.0) || !(p->tau_grad >= 0.0))
     return set_err(ctx, HGF_EINVAL, "alpha must be in [0, 1] and thresholds >= 0");
   if (p->direction != 1 && p->direction != -1)
     return set_err(ctx, HGF_EINVAL, "direction must be +1 or -1");
+  return HGF_OK;
+}
+
+// Stereo aggregation with ctx->mu held and arguments checked.
+hgf_status aggregate_stereo_locked(hgf_ctx *ctx, const hgf_guidance *g, const float *other, int L,
+                                   const hgf_cost_params *p, void *filtered, int32_t *labels,
+                                   float *best, cudaStream_t s) {
   if (!aggregate_fits(g))
     return set_err(ctx, HGF_EUNSUPPORTED, "stereo aggregation needs 2r+1 < %d", kStripThreads);
-  cudaStream_t s = (cudaStream_t)stream;
-  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   const size_t HW = (size_t)g->H * g->W;
   AggregatePlan plan = plan_aggregate(g, L, ctx->tuning, ctx->num_sms);
-  st = grow(ctx, ctx->ws_coef, aggregate_coef_bytes(g, plan), s);
+  hgf_status st = grow(ctx, ctx->ws_coef, aggregate_coef_bytes(g, plan), s);
   if (st == HGF_OK) st = grow(ctx, ctx->ws_keys, HW * sizeof(unsigned long long), s);
   if (st == HGF_OK) st = grow(ctx, ctx->ws_grad, 2 * HW * sizeof(float), s);
   if (st != HGF_OK) return st;
@@ -597,7 +599,120 @@ hgf_status hgf_aggregate_stereo(hgf_ctx *ctx, const hgf_guidance *g, const float
     e = launch_aggregate(g, nullptr, kCostStereo, L, (float *)filtered, labels, best,
                          (float *)ctx->ws_coef.ptr, (unsigned long long *)ctx->ws_keys.ptr, plan,
                          s, &ctx->prof, &src);
-  if (e != cudaSuccess) return cuda_fail_locked(ctx, e, "hgf_aggregate_stereo");
+  if (e != cudaSuccess) return cuda_fail_locked(ctx, e, "stereo aggregation");
+  return HGF_OK;
+}
+
+// A host-path guidance handle of this shape, reallocated when the shape or parameters change.
+hgf_status host_guidance_for(hgf_ctx *ctx, hgf_guidance **slot, int C, int H, int W, int n,
+                             const hgf_params *params, cudaStream_t s) {
+  if (same_shape(*slot, C, H, W, params)) return HGF_OK;
+  if (*slot) {
+    cudaStreamSynchronize(s);
+    cudaFree((*slot)->rec);
+    delete *slot;
+    *slot = nullptr;
+  }
+  return alloc_guidance(ctx, C, H, W, n, params, slot);
+}
+
+}  // namespace
+
+hgf_status hgf_aggregate_stereo(hgf_ctx *ctx, const hgf_guidance *g, const float *other, int L,
+                                const hgf_cost_params *p, void *filtered, int filtered_dtype,
+                                int32_t *labels, float *best, void *stream) {
+  NvtxRange nvtx_range("hgf_aggregate_stereo");
+  hgf_status st = enter(ctx);
+  if (st != HGF_OK) return st;
+  if (!other || !p) return set_err(ctx, HGF_EINVAL, "NULL argument");
+  // the cost is made here, not read: check the outputs with a stand-in cost pointer
+  st = check_outputs(ctx, g, other, HGF_F32, L, filtered, filtered_dtype, labels, best);
+  if (st != HGF_OK) return st;
+  st = check_cost_params(ctx, p);
+  if (st != HGF_OK) return st;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  return aggregate_stereo_locked(ctx, g, other, L, p, filtered, labels, best,
+                                 (cudaStream_t)stream);
+}
+
+hgf_status hgf_stereo_host(hgf_ctx *ctx, const float *left, const float *right, int C, int H,
+                           int W, int L, const hgf_params *params, const hgf_cost_params *cost,
+                           int refine, int threshold, int32_t *disparity, void *stream) {
+  NvtxRange nvtx_range("hgf_stereo_host");
+  hgf_status st = enter(ctx);
+  if (st != HGF_OK) return st;
+  if (!left || !right || !cost || !disparity) return set_err(ctx, HGF_EINVAL, "NULL argument");
+  if (L < 1) return set_err(ctx, HGF_EINVAL, "L must be >= 1");
+  if (refine != 0 && refine != 1) return set_err(ctx, HGF_EINVAL, "refine must be 0 or 1");
+  if (threshold < 0) return set_err(ctx, HGF_EINVAL, "threshold must be >= 0");
+  int n = 0;
+  st = check_params(ctx, C, H, W, params, &n);
+  if (st != HGF_OK) return st;
+  hgf_cost_params cp = *cost;
+  cp.direction = 1;
+  st = check_cost_params(ctx, &cp);
+  if (st != HGF_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t HW = (size_t)H * W;
+  const size_t img_b = ((size_t)C * HW * 4 + 255) / 256 * 256;
+  const size_t out_b = (HW * 4 + 255) / 256 * 256;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  st = grow(ctx, ctx->ws_io, 2 * img_b + 3 * out_b + out_b, s);
+  if (st != HGF_OK) return st;
+  char *base = (char *)ctx->ws_io.ptr;
+  float *left_d = (float *)base;
+  float *right_d = (float *)(base + img_b);
+  int32_t *lab_l = (int32_t *)(base + 2 * img_b);
+  int32_t *lab_r = (int32_t *)(base + 2 * img_b + out_b);
+  int32_t *refined = (int32_t *)(base + 2 * img_b + 2 * out_b);
+  uint8_t *keep = (uint8_t *)(base + 2 * img_b + 3 * out_b);
+  // the right view goes over the library's second stream while the left guidance is prepared
+  cudaError_t e = cudaSuccess;
+  if (!ctx->io_stream) e = cudaStreamCreateWithFlags(&ctx->io_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !ctx->io_fork)
+    e = cudaEventCreateWithFlags(&ctx->io_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess && !ctx->io_done)
+    e = cudaEventCreateWithFlags(&ctx->io_done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->io_fork, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->io_stream, ctx->io_fork, 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(right_d, right, (size_t)C * HW * 4, cudaMemcpyHostToDevice,
+                        ctx->io_stream);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->io_done, ctx->io_stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(left_d, left, (size_t)C * HW * 4, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail_locked(ctx, e, "hgf_stereo_host upload");
+  st = host_guidance_for(ctx, &ctx->host_guidance, C, H, W, n, params, s);
+  if (st == HGF_OK && refine)
+    st = host_guidance_for(ctx, &ctx->host_guidance_right, C, H, W, n, params, s);
+  if (st != HGF_OK) return st;
+  st = prepare_locked(ctx, ctx->host_guidance, left_d, s);
+  if (st != HGF_OK) return st;
+  e = cudaStreamWaitEvent(s, ctx->io_done, 0);
+  if (e != cudaSuccess) return cuda_fail_locked(ctx, e, "hgf_stereo_host upload wait");
+  st = aggregate_stereo_locked(ctx, ctx->host_guidance, right_d, L, &cp, nullptr, lab_l, nullptr,
+                               s);
+  if (st != HGF_OK) return st;
+  const int32_t *result = lab_l;
+  if (refine) {
+    st = prepare_locked(ctx, ctx->host_guidance_right, right_d, s);
+    if (st != HGF_OK) return st;
+    hgf_cost_params cr = cp;
+    cr.direction = -1;
+    st = aggregate_stereo_locked(ctx, ctx->host_guidance_right, left_d, L, &cr, nullptr, lab_r,
+                                 nullptr, s);
+    if (st != HGF_OK) return st;
+    e = launch_refine_lr(lab_l, lab_r, H, W, threshold, refined, keep, s, &ctx->prof);
+    if (e != cudaSuccess) return cuda_fail_locked(ctx, e, "hgf_stereo_host refine");
+    result = refined;
+  }
+  e = cudaMemcpyAsync(disparity, result, HW * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail_locked(ctx, e, "hgf_stereo_host download");
+  int status = 0;
+  e = read_device_status(&status, true);
+  if (e != cudaSuccess) return cuda_fail_locked(ctx, e, "hgf_stereo_host status");
+  if (status != 0) return set_err(ctx, HGF_ETIMEOUT, "a bounded wait in a kernel ran out");
   return HGF_OK;
 }
 

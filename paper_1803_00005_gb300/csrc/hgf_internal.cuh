@@ -195,7 +195,8 @@ struct hgf_ctx {
   // hgf_filter_host uploads the cost volume on io_stream while the guidance precompute runs
   cudaStream_t io_stream = nullptr;
   cudaEvent_t io_fork = nullptr, io_done = nullptr;
-  hgf_guidance *host_guidance = nullptr;  // reused by hgf_filter_host
+  hgf_guidance *host_guidance = nullptr;        // reused by hgf_filter_host, hgf_stereo_host
+  hgf_guidance *host_guidance_right = nullptr;  // right view of hgf_stereo_host (refinement)
   hgf_tuning tuning{0, 0, 0, 0};
   int num_sms = 0;
   hgf::Profiler prof;

@@ -38,7 +38,7 @@ EXPORTED = [
     "hgf_serve_wait", "hgf_serve_stats", "hgf_serve_inject_alloc_failures", "hgf_serve_destroy",
     "hgf_batch_create", "hgf_batch_run", "hgf_batch_launch_graph", "hgf_batch_destroy",
     "hgf_device_status", "hgf_batched_inverse", "hgf_cost_volume", "hgf_aggregate_stereo",
-    "hgf_refine_lr", "hgf_autotune", "hgf_watchdog_probe",
+    "hgf_refine_lr", "hgf_autotune", "hgf_watchdog_probe", "hgf_stereo_host",
 ]
 
 
@@ -140,6 +140,8 @@ def lib():
         "hgf_launch_count": (c_int, [vp, P(ctypes.c_ulonglong)]),
         "hgf_device_status": (c_int, [vp, P(c_int), c_int]),
         "hgf_watchdog_probe": (c_int, [vp, c_int, vp]),
+        "hgf_stereo_host": (c_int, [vp, vp, vp, c_int, c_int, c_int, c_int, P(hgf_params),
+                                    P(hgf_cost_params), c_int, c_int, vp, vp]),
         "hgf_batched_inverse": (c_int, [vp, vp, c_int, c_int, c_double, c_int, c_int, vp, vp]),
         "hgf_cost_volume": (c_int, [vp, vp, vp, c_int, c_int, c_int, c_int, P(hgf_cost_params),
                                     c_int, vp, vp]),
@@ -445,6 +447,29 @@ def autotune_cached(ctx, g, cost, labels, cache_path, reps=3, stream=None):
         json.dump(cache, f, indent=1, sort_keys=True)
     os.replace(tmp, cache_path)
     return tuning, False
+
+
+def hgf_stereo_host(ctx, left, right, L, params, refine=True, threshold=1, out=None,
+                    alpha=0.9, tau_color=0.028, tau_grad=0.008, stream=None):
+    """Stereo pipeline from host memory: left/right float32 (C, H, W) numpy arrays (pinned or
+    pageable) in, int32 (H, W) disparity numpy array out (written into `out` when given)."""
+    import numpy as np
+    left = np.ascontiguousarray(left, dtype=np.float32)
+    right = np.ascontiguousarray(right, dtype=np.float32)
+    if left.shape != right.shape or left.ndim != 3:
+        raise ValueError("left and right must be (C, H, W) arrays of the same shape")
+    C, H, W = left.shape
+    if out is None:
+        out = np.empty((H, W), dtype=np.int32)
+    if out.dtype != np.int32 or out.shape != (H, W) or not out.flags["C_CONTIGUOUS"]:
+        raise ValueError("out must be a contiguous int32 (H, W) array")
+    cp = hgf_cost_params(alpha=float(alpha), tau_color=float(tau_color), tau_grad=float(tau_grad),
+                         direction=1)
+    _check(ctx, lib().hgf_stereo_host(ctx, left.ctypes.data, right.ctypes.data, C, H, W, int(L),
+                                      ctypes.byref(params), ctypes.byref(cp),
+                                      1 if refine else 0, int(threshold), out.ctypes.data,
+                                      _stream(stream)))
+    return out
 
 
 def hgf_watchdog_probe(ctx, limit_us, stream=None):

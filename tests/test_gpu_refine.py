@@ -70,3 +70,31 @@ def test_stereo_pipeline_left_right_refine(ctx):
     err_ref = np.mean(np.abs(want - disp) > 1)
     print(f"\nbad pixels (>1): WTA {err_wta:.3f}, refined {err_ref:.3f}, kept {wkeep.mean():.3f}")
     assert err_wta < 0.5 and err_ref < 0.5
+
+
+def test_stereo_host_pipeline_matches_device_calls(ctx):
+    """hgf_stereo_host (host views in, disparity out) gives exactly the labels of the device-side
+    calls it stands for: aggregate_stereo of the left view, and with refinement also of the
+    right view followed by refine_lr."""
+    torch = torch_cuda()
+    from paper_1803_00005_gb300 import hgf
+    W, H, L = 257, 143, 24
+    left, right, _ = synth.stereo_pair(W, H, L, 31)
+    l32, r32 = left.astype(np.float32), right.astype(np.float32)
+    p = hgf.make_params(degree=2, r=9, eps=1e-4)
+    raw = hgf.hgf_stereo_host(ctx, l32, r32, L, p, refine=False)
+    ref = hgf.hgf_stereo_host(ctx, l32, r32, L, p, refine=True, threshold=1)
+    Lt, Rt = torch.from_numpy(l32).cuda(), torch.from_numpy(r32).cuda()
+    gl, gr = hgf.hgf_prepare(ctx, Lt, p), hgf.hgf_prepare(ctx, Rt, p)
+    try:
+        dl = torch.empty((H, W), dtype=torch.int32, device="cuda")
+        dr = torch.empty_like(dl)
+        hgf.hgf_aggregate_stereo(ctx, gl, Rt, L, labels=dl, direction=1)
+        hgf.hgf_aggregate_stereo(ctx, gr, Lt, L, labels=dr, direction=-1)
+        out, _ = hgf.hgf_refine_lr(ctx, dl, dr, 1)
+        torch.cuda.synchronize()
+    finally:
+        hgf.hgf_guidance_release(gl)
+        hgf.hgf_guidance_release(gr)
+    assert np.array_equal(raw, dl.cpu().numpy())
+    assert np.array_equal(ref, out.cpu().numpy())
