@@ -13,9 +13,12 @@
 //   k_apply: vertical running sums of (b, a_1..a_n), horizontal window sums,
 //            q = sum_i A(a_i) G_i + A(b), and one packed 64-bit atomicMin per pixel (cost in the
 //            high word, label in the low word: lowest cost, then lowest label).
-// Every input row is read from device memory once: each thread keeps its column's last 2r+1 rows
-// in a private shared-memory ring (the row leaving the vertical window is subtracted from there)
-// and loads rows two steps ahead into registers, so the load latency overlaps two steps of work.
+// Rows are loaded two steps ahead into registers (a three-buffer rotation), so the load latency
+// overlaps two steps of work; the row leaving the vertical window is re-read, still in L2 (or,
+// in the ring instantiations, kept in a per-thread shared-memory ring). k_coef stages each row's
+// block of inverse records in shared memory with one bulk asynchronous copy. The paper's form
+// (HGF_FORM_PAPER) changes only k_coef's per-pixel solve; the stereo instantiation computes the
+// cost from the two views instead of reading a cost volume.
 // Windows are clipped at the image border: samples outside the image never enter a sum and the
 // means divide by the in-image count N(x, y).
 #pragma once
@@ -41,8 +44,8 @@ using strip::window;
 // bulk asynchronous copies and bounded mbarrier waits: hgf_mbarrier.cuh
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // a bounded wait gives up after 1 s
 
-// Strip-tiled inverse records (n <= 9) are staged in shared memory, a double buffer filled one
-// row ahead by bulk copies; pixel-major ones (n = 19) are loaded by phase C itself.
+// Strip-tiled inverse records (n <= 9) are staged in shared memory by bulk copies
+// (kRecordBuffers blocks per CTA); pixel-major ones (n = 19) are loaded by phase C itself.
 template <int B>
 __host__ __device__ constexpr bool stage_records() { return records_strip_tiled(basis_n(B)); }
 
