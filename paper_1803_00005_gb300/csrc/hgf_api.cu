@@ -517,22 +517,24 @@ hgf_status hgf_filter_host(hgf_ctx *ctx, const float *img, int C, int H, int W,
   void *cost_d = base + img_b;
   int32_t *labels_d = (int32_t *)(base + img_b + cost_b);
   float *best_d = (float *)(base + img_b + cost_b + out_b);
-  // the cost volume (the bulk of the upload) goes over a second stream, concurrently with the
-  // image upload and the guidance precompute; the aggregation waits for it
+  // the image goes first (the guidance precompute needs only it); the cost volume, the bulk of
+  // the upload, follows on a second stream while the precompute runs, and the aggregation waits
+  // for it (queued after the image, so that copy engines serving the streams in order never make
+  // the precompute wait for the volume)
   cudaError_t e = cudaSuccess;
   if (!ctx->io_stream) e = cudaStreamCreateWithFlags(&ctx->io_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess && !ctx->io_fork)
     e = cudaEventCreateWithFlags(&ctx->io_fork, cudaEventDisableTiming);
   if (e == cudaSuccess && !ctx->io_done)
     e = cudaEventCreateWithFlags(&ctx->io_done, cudaEventDisableTiming);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(img_d, img, (size_t)C * HW * 4, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaEventRecord(ctx->io_fork, s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->io_stream, ctx->io_fork, 0);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(cost_d, cost, (size_t)L * HW * dtype_size(cost_dtype),
                         cudaMemcpyHostToDevice, ctx->io_stream);
   if (e == cudaSuccess) e = cudaEventRecord(ctx->io_done, ctx->io_stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(img_d, img, (size_t)C * HW * 4, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail_locked(ctx, e, "hgf_filter_host upload");
   if (!same_shape(ctx->host_guidance, C, H, W, params)) {
     if (ctx->host_guidance) {
@@ -666,21 +668,22 @@ hgf_status hgf_stereo_host(hgf_ctx *ctx, const float *left, const float *right, 
   int32_t *lab_r = (int32_t *)(base + 2 * img_b + out_b);
   int32_t *refined = (int32_t *)(base + 2 * img_b + 2 * out_b);
   uint8_t *keep = (uint8_t *)(base + 2 * img_b + 3 * out_b);
-  // the right view goes over the library's second stream while the left guidance is prepared
+  // the left view first; the right view follows on the library's second stream while the left
+  // guidance is prepared
   cudaError_t e = cudaSuccess;
   if (!ctx->io_stream) e = cudaStreamCreateWithFlags(&ctx->io_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess && !ctx->io_fork)
     e = cudaEventCreateWithFlags(&ctx->io_fork, cudaEventDisableTiming);
   if (e == cudaSuccess && !ctx->io_done)
     e = cudaEventCreateWithFlags(&ctx->io_done, cudaEventDisableTiming);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(left_d, left, (size_t)C * HW * 4, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaEventRecord(ctx->io_fork, s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->io_stream, ctx->io_fork, 0);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(right_d, right, (size_t)C * HW * 4, cudaMemcpyHostToDevice,
                         ctx->io_stream);
   if (e == cudaSuccess) e = cudaEventRecord(ctx->io_done, ctx->io_stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(left_d, left, (size_t)C * HW * 4, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail_locked(ctx, e, "hgf_stereo_host upload");
   st = host_guidance_for(ctx, &ctx->host_guidance, C, H, W, n, params, s);
   if (st == HGF_OK && refine)
