@@ -170,6 +170,23 @@ hgf_status hgf_aggregate_plain(hgf_ctx *ctx, const hgf_guidance *g, const void *
 hgf_status hgf_wta(hgf_ctx *ctx, const void *filtered, int dtype, int L, int H, int W,
                    int32_t *labels, float *best, void *stream);
 
+/* hgf_aggregate with the WTA margin (Sec. 1 WTA, with a confidence output the paper does not
+ * have): margin = (second-smallest filtered cost) - (smallest), per pixel, in float32; +inf when
+ * L = 1; 0 when two labels tie for the minimum; NaN when the two smallest are both +inf (NaN
+ * filtered costs count as +inf, as for the labels). labels, best: as for hgf_aggregate (either may
+ * be NULL); margin: device float32 H x W, required. The fused path keeps a second 64-bit key per
+ * pixel (the keys workspace doubles) and returns the old key from its atomic minimum; windows too
+ * wide for the fused kernels take the plain path and hgf_wta_margin. Same errors as hgf_aggregate,
+ * plus HGF_EINVAL for a NULL margin. */
+hgf_status hgf_aggregate_margin(hgf_ctx *ctx, const hgf_guidance *g, const void *cost,
+                                int cost_dtype, int L, int32_t *labels, float *best,
+                                float *margin, void *stream);
+
+/* hgf_wta with the margin (as for hgf_aggregate_margin) over an already-filtered volume: filtered
+ * device L x H x W (HGF_F32); labels, best may be NULL; margin device float32 H x W, required. */
+hgf_status hgf_wta_margin(hgf_ctx *ctx, const void *filtered, int dtype, int L, int H, int W,
+                          int32_t *labels, float *best, float *margin, void *stream);
+
 /* End to end from host memory: copies img (host, C x H x W float32) and cost (host, L x H x W of
  * cost_dtype) to the device, prepares the guidance, aggregates with WTA and copies labels (host
  * int32 H x W, may be NULL) and best (host float32 H x W, may be NULL) back; returns after the

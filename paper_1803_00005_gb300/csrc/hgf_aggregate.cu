@@ -15,32 +15,50 @@ constexpr int NT = kStripThreads;
 constexpr int kRowStride = NT + 4;  // shared row stride of the fused kernels' scan buffers
 __device__ int g_device_status = 0;  // nonzero after a bounded wait in a kernel ran out
 
-__global__ void k_wta_finalize(const unsigned long long *__restrict__ keys, int HW,
-                               int32_t *__restrict__ labels, float *__restrict__ best) {
+// Unpacks the per-pixel WTA keys. With `second` (the smallest key other than the winner's, all
+// ones while a pixel has seen one label only), margin = second-best cost - best cost, +inf for a
+// single label.
+__global__ void k_wta_finalize(const unsigned long long *__restrict__ keys,
+                               const unsigned long long *__restrict__ second, int HW,
+                               int32_t *__restrict__ labels, float *__restrict__ best,
+                               float *__restrict__ margin) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= HW) return;
   unsigned long long key = keys[p];
   if (labels) labels[p] = (int32_t)(unsigned int)(key & 0xffffffffull);
   if (best) best[p] = wta_key_value(key);
+  if (margin) {
+    const unsigned long long k2 = second[p];
+    margin[p] = k2 == ~0ull ? __int_as_float(0x7f800000) : wta_key_value(k2) - wta_key_value(key);
+  }
 }
 
-// Standalone WTA over a filtered volume: one thread per pixel scanning the labels in order.
+// Standalone WTA over a filtered volume: one thread per pixel scanning the labels in order,
+// keeping the best and second-best values (a tie with the best gives margin 0).
 __global__ void k_wta_volume(const float *__restrict__ q, int L, int HW,
-                             int32_t *__restrict__ labels, float *__restrict__ best) {
+                             int32_t *__restrict__ labels, float *__restrict__ best,
+                             float *__restrict__ margin) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= HW) return;
-  float b = 0.f;
+  const float inf = __int_as_float(0x7f800000);
+  float b = 0.f, b2 = inf;
   int lb = 0;
   for (int l = 0; l < L; ++l) {
     float v = q[(size_t)l * HW + p];
-    if (v != v) v = __int_as_float(0x7f800000);
-    if (l == 0 || v < b) {
+    if (v != v) v = inf;
+    if (l == 0) {
+      b = v;
+    } else if (v < b) {
+      b2 = b;
       b = v;
       lb = l;
+    } else if (v < b2) {
+      b2 = v;
     }
   }
   if (labels) labels[p] = lb;
   if (best) best[p] = b;
+  if (margin) margin[p] = L == 1 ? inf : b2 - b;
 }
 
 // Watchdog probe: one CTA waits, bounded, on an mbarrier that nothing arrives on (it expects one
@@ -153,13 +171,17 @@ size_t aggregate_coef_bytes(const hgf_guidance *g, const AggregatePlan &p) {
 
 cudaError_t launch_aggregate(const hgf_guidance *g, const void *cost, int cost_dtype, int L,
                              float *filtered, int32_t *labels, float *best, float *coef_ws,
-                             unsigned long long *keys, const AggregatePlan &p, cudaStream_t s,
-                             Profiler *prof, const StereoSource *stereo) {
+                             unsigned long long *keys, const AggregatePlan &plan,
+                             cudaStream_t s, Profiler *prof, const StereoSource *stereo,
+                             float *margin) {
   const int HW = g->H * g->W;
-  const bool want_wta = labels || best;
+  const bool want_wta = labels || best || margin;
   unsigned long long *k = want_wta ? keys : nullptr;
+  AggregatePlan p = plan;
+  p.second = margin != nullptr;  // the keys workspace then holds 2 x H x W keys
   if (k) {
-    cudaError_t e = cudaMemsetAsync(k, 0xff, (size_t)HW * sizeof(unsigned long long), s);
+    cudaError_t e = cudaMemsetAsync(k, 0xff, (size_t)HW * (p.second ? 2 : 1) *
+                                                 sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
   }
   if (cost_dtype == kCostStereo && !stereo) return cudaErrorInvalidValue;
@@ -176,16 +198,17 @@ cudaError_t launch_aggregate(const hgf_guidance *g, const void *cost, int cost_d
   if (e != cudaSuccess) return e;
   if (k) {
     LaunchScope ls(prof, "k_wta_finalize", s);
-    k_wta_finalize<<<(HW + 255) / 256, 256, 0, s>>>(k, HW, labels, best);
+    k_wta_finalize<<<(HW + 255) / 256, 256, 0, s>>>(k, p.second ? k + HW : nullptr, HW, labels,
+                                                    best, margin);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_wta(const float *filtered, int L, int H, int W, int32_t *labels, float *best,
-                       cudaStream_t s, Profiler *prof) {
+                       cudaStream_t s, Profiler *prof, float *margin) {
   int HW = H * W;
   LaunchScope ls(prof, "k_wta_volume", s);
-  k_wta_volume<<<(HW + 255) / 256, 256, 0, s>>>(filtered, L, HW, labels, best);
+  k_wta_volume<<<(HW + 255) / 256, 256, 0, s>>>(filtered, L, HW, labels, best, margin);
   return cudaGetLastError();
 }
 

@@ -193,7 +193,7 @@ hgf_status check_outputs(hgf_ctx *ctx, const hgf_guidance *g, const void *cost, 
 
 hgf_status aggregate_locked(hgf_ctx *ctx, const hgf_guidance *g, const void *cost,
                             int cost_dtype, int L, void *filtered, int32_t *labels, float *best,
-                            cudaStream_t s) {
+                            cudaStream_t s, float *margin = nullptr) {
   if (!aggregate_fits(g)) {
     if (g->form != HGF_FORM_CENTRED)
       return set_err(ctx, HGF_EUNSUPPORTED, "the paper form needs 2r+1 < %d", kStripThreads);
@@ -206,18 +206,20 @@ hgf_status aggregate_locked(hgf_ctx *ctx, const hgf_guidance *g, const void *cos
     if (st != HGF_OK) return st;
     float *q = filtered ? (float *)filtered : (float *)((char *)ctx->ws_plain.ptr + need);
     cudaError_t e = launch_aggregate_plain(g, cost, cost_dtype, L, q, labels, best,
-                                           ctx->ws_plain.ptr, chunk, s, &ctx->prof);
+                                           ctx->ws_plain.ptr, chunk, s, &ctx->prof, margin);
     if (e != cudaSuccess) return cuda_fail_locked(ctx, e, "hgf_aggregate (wide window)");
     return HGF_OK;
   }
   AggregatePlan plan = plan_aggregate(g, L, ctx->tuning, ctx->num_sms);
   hgf_status st = grow(ctx, ctx->ws_coef, aggregate_coef_bytes(g, plan), s);
   if (st == HGF_OK)
-    st = grow(ctx, ctx->ws_keys, (size_t)g->H * g->W * sizeof(unsigned long long), s);
+    st = grow(ctx, ctx->ws_keys,
+              (size_t)g->H * g->W * (margin ? 2 : 1) * sizeof(unsigned long long), s);
   if (st != HGF_OK) return st;
   cudaError_t e = launch_aggregate(g, cost, cost_dtype, L, (float *)filtered, labels, best,
                                    (float *)ctx->ws_coef.ptr,
-                                   (unsigned long long *)ctx->ws_keys.ptr, plan, s, &ctx->prof);
+                                   (unsigned long long *)ctx->ws_keys.ptr, plan, s, &ctx->prof,
+                                   nullptr, margin);
   if (e != cudaSuccess) return cuda_fail_locked(ctx, e, "hgf_aggregate");
   return HGF_OK;
 }
@@ -453,6 +455,20 @@ hgf_status hgf_aggregate(hgf_ctx *ctx, const hgf_guidance *g, const void *cost, 
                           (cudaStream_t)stream);
 }
 
+hgf_status hgf_aggregate_margin(hgf_ctx *ctx, const hgf_guidance *g, const void *cost,
+                                int cost_dtype, int L, int32_t *labels, float *best,
+                                float *margin, void *stream) {
+  NvtxRange nvtx_range("hgf_aggregate_margin");
+  hgf_status st = enter(ctx);
+  if (st != HGF_OK) return st;
+  if (!margin) return set_err(ctx, HGF_EINVAL, "margin is NULL");
+  st = check_outputs(ctx, g, cost, cost_dtype, L, nullptr, HGF_F32, labels, best ? best : margin);
+  if (st != HGF_OK) return st;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  return aggregate_locked(ctx, g, cost, cost_dtype, L, nullptr, labels, best,
+                          (cudaStream_t)stream, margin);
+}
+
 hgf_status hgf_aggregate_plain(hgf_ctx *ctx, const hgf_guidance *g, const void *cost,
                                int cost_dtype, int L, void *filtered, int filtered_dtype,
                                int32_t *labels, float *best, void *stream) {
@@ -489,6 +505,21 @@ hgf_status hgf_wta(hgf_ctx *ctx, const void *filtered, int dtype, int L, int H, 
   cudaError_t e = launch_wta((const float *)filtered, L, H, W, labels, best,
                              (cudaStream_t)stream, &ctx->prof);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "hgf_wta");
+  return HGF_OK;
+}
+
+hgf_status hgf_wta_margin(hgf_ctx *ctx, const void *filtered, int dtype, int L, int H, int W,
+                          int32_t *labels, float *best, float *margin, void *stream) {
+  NvtxRange nvtx_range("hgf_wta_margin");
+  hgf_status st = enter(ctx);
+  if (st != HGF_OK) return st;
+  if (!filtered || !margin) return set_err(ctx, HGF_EINVAL, "NULL argument");
+  if (dtype != HGF_F32) return set_err(ctx, HGF_EINVAL, "hgf_wta_margin takes HGF_F32 volumes");
+  if (L < 1 || H < 1 || W < 1) return set_err(ctx, HGF_EINVAL, "bad shape");
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  cudaError_t e = launch_wta((const float *)filtered, L, H, W, labels, best,
+                             (cudaStream_t)stream, &ctx->prof, margin);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "hgf_wta_margin");
   return HGF_OK;
 }
 

@@ -407,6 +407,7 @@ __global__ void __launch_bounds__(NT) k_apply(const float *__restrict__ coef, in
                                               const float *__restrict__ img,
                                               const float *__restrict__ shift,
                                               unsigned long long *__restrict__ keys,
+                                              unsigned long long *__restrict__ keys2,
                                               float *__restrict__ filtered, int l_first,
                                               int band_rows) {
   constexpr int NG = basis_n(B), C1 = NG + 1, NC = basis_channels_in(B), CP = coef_floats(NG);
@@ -529,7 +530,17 @@ __global__ void __launch_bounds__(NT) k_apply(const float *__restrict__ coef, in
       q *= invN;
       const int label = l_first + k;
       if (filtered) filtered[(size_t)label * HW + pix] = q;
-      if (keys) atomicMin(keys + pix, wta_key(q, label));
+      if (keys) {
+        const unsigned long long key = wta_key(q, label);
+        if (keys2) {
+          // second-smallest key: every key but the final minimum reaches keys2 exactly once,
+          // either directly (it lost to the minimum so far) or when a smaller key displaces it
+          const unsigned long long old = atomicMin(keys + pix, key);
+          atomicMin(keys2 + pix, old > key ? old : key);
+        } else {
+          atomicMin(keys + pix, key);
+        }
+      }
     }
   };
   for (int s = s_begin; s < s_end; s += 3) {
@@ -583,6 +594,7 @@ static int resident_ctas(Kern k, size_t smem) {
 template <int B, int K, bool COMP>
 cudaError_t launch_chunk(const hgf_guidance *g, const void *cost, int cost_dtype, int l_first,
                          int nc, float *filtered, float *coef_ws, unsigned long long *keys,
+                         unsigned long long *keys2,
                          int band_rows, bool apply_ring, int nominal, int *status,
                          const StereoSource &stereo, cudaStream_t s, Profiler *prof) {
   const int H = g->H, W = g->W, r = g->r;
@@ -638,7 +650,8 @@ cudaError_t launch_chunk(const hgf_guidance *g, const void *cost, int cost_dtype
                                                                         ring_sm));
         dim3 grid(nc, strips, (H + rows - 1) / rows);
         k_apply<B, true, false><<<grid, NT, ring_sm, s>>>(coef_ws, H, W, r, g->img, g->shift,
-                                                          keys, filtered, l_first, rows);
+                                                          keys, keys2, filtered, l_first,
+                                                          rows);
       }
     }
     if (!ringed) {
@@ -652,7 +665,7 @@ cudaError_t launch_chunk(const hgf_guidance *g, const void *cost, int cost_dtype
                                                                       sm));
       dim3 grid(nc, strips, (H + rows - 1) / rows);
       k_apply<B, false, COMP><<<grid, NT, sm, s>>>(coef_ws, H, W, r, g->img, g->shift, keys,
-                                                   filtered, l_first, rows);
+                                                   keys2, filtered, l_first, rows);
     }
   }
   return cudaGetLastError();
@@ -668,19 +681,20 @@ cudaError_t launch_basis(const hgf_guidance *g, const void *cost, int cost_dtype
                          const AggregatePlan &p, int *status, const StereoSource &stereo,
                          cudaStream_t s, Profiler *prof) {
   cudaError_t e = cudaSuccess;
+  unsigned long long *keys2 = keys && p.second ? keys + (size_t)g->H * g->W : nullptr;
   for (int l0 = 0; l0 < L && e == cudaSuccess; l0 += p.chunk) {
     const int nc = std::min(p.chunk, L - l0);
     if (g->compensated)  // compensated sums: two labels per pass only
       e = launch_chunk<B, 2, true>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys,
-                                   p.band_rows, false, p.nominal, status, stereo, s, prof);
+                                   keys2, p.band_rows, false, p.nominal, status, stereo, s, prof);
     else if (p.K == 4)
-      e = launch_chunk<B, 4, false>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys, p.band_rows,
+      e = launch_chunk<B, 4, false>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys, keys2, p.band_rows,
                              p.apply_ring, p.nominal, status, stereo, s, prof);
     else if (p.K == 8)
-      e = launch_chunk<B, 8, false>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys, p.band_rows,
+      e = launch_chunk<B, 8, false>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys, keys2, p.band_rows,
                              p.apply_ring, p.nominal, status, stereo, s, prof);
     else
-      e = launch_chunk<B, 2, false>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys, p.band_rows,
+      e = launch_chunk<B, 2, false>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys, keys2, p.band_rows,
                              p.apply_ring, p.nominal, status, stereo, s, prof);
   }
   return e;

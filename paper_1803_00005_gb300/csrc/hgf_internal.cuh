@@ -243,19 +243,22 @@ struct AggregatePlan {
   bool apply_ring;  // output kernel keeps the outgoing rows in a shared-memory ring
   int nominal;      // label count the band heights are planned for: min(64, L rounded up to
                     // even), the same for every chunk of a call so chunking never changes a result
+  bool second = false;  // WTA also keeps each pixel's second-smallest key, at keys + H*W
 };
 AggregatePlan plan_aggregate(const hgf_guidance *g, int L, const hgf_tuning &t, int num_sms);
 size_t aggregate_coef_bytes(const hgf_guidance *g, const AggregatePlan &p);
 cudaError_t launch_aggregate(const hgf_guidance *g, const void *cost, int cost_dtype, int L,
                              float *filtered, int32_t *labels, float *best, float *coef_ws,
                              unsigned long long *keys, const AggregatePlan &p, cudaStream_t s,
-                             Profiler *prof, const StereoSource *stereo = nullptr);
+                             Profiler *prof, const StereoSource *stereo = nullptr,
+                             float *margin = nullptr);
 size_t plain_workspace_bytes(const hgf_guidance *g, int L, int *chunk_out);
 cudaError_t launch_aggregate_plain(const hgf_guidance *g, const void *cost, int cost_dtype,
                                    int L, float *filtered, int32_t *labels, float *best,
-                                   void *ws, int chunk, cudaStream_t s, Profiler *prof);
+                                   void *ws, int chunk, cudaStream_t s, Profiler *prof,
+                                   float *margin = nullptr);
 cudaError_t launch_wta(const float *filtered, int L, int H, int W, int32_t *labels, float *best,
-                       cudaStream_t s, Profiler *prof);
+                       cudaStream_t s, Profiler *prof, float *margin = nullptr);
 bool aggregate_supported(int n);
 // Guidance handle allocation (cudaMalloc) after argument checks; free_guidance releases it.
 hgf_status alloc_guidance_checked(hgf_ctx *ctx, int C, int H, int W, const hgf_params *p,

@@ -110,7 +110,7 @@ size_t plain_workspace_bytes(const hgf_guidance *g, int L, int *chunk_out) {
 
 cudaError_t launch_aggregate_plain(const hgf_guidance *g, const void *cost, int cost_dtype, int L,
                                    float *q, int32_t *labels, float *best, void *ws, int chunk,
-                                   cudaStream_t s, Profiler *prof) {
+                                   cudaStream_t s, Profiler *prof, float *margin) {
   const int H = g->H, W = g->W, n = g->n, r = g->r;
   const size_t HW = (size_t)H * W;
   float *A = (float *)ws;
@@ -167,7 +167,7 @@ cudaError_t launch_aggregate_plain(const hgf_guidance *g, const void *cost, int 
       p_output<<<nblk(Lp * HW), 256, 0, s>>>(B, g->G, n, H, W, r, Lp, q + (size_t)l0 * HW);
     }
   }
-  if (labels || best) return launch_wta(q, L, H, W, labels, best, s, prof);
+  if (labels || best || margin) return launch_wta(q, L, H, W, labels, best, s, prof, margin);
   return cudaGetLastError();
 }
 

@@ -39,6 +39,7 @@ EXPORTED = [
     "hgf_batch_create", "hgf_batch_run", "hgf_batch_launch_graph", "hgf_batch_destroy",
     "hgf_device_status", "hgf_batched_inverse", "hgf_cost_volume", "hgf_aggregate_stereo",
     "hgf_refine_lr", "hgf_autotune", "hgf_watchdog_probe", "hgf_stereo_host",
+    "hgf_aggregate_margin", "hgf_wta_margin",
 ]
 
 
@@ -133,6 +134,8 @@ def lib():
         "hgf_batch_launch_graph": (c_int, [vp, vp]),
         "hgf_batch_destroy": (c_int, [vp]),
         "hgf_wta": (c_int, [vp, vp, c_int, c_int, c_int, c_int, vp, vp, vp]),
+        "hgf_wta_margin": (c_int, [vp, vp, c_int, c_int, c_int, c_int, vp, vp, vp, vp]),
+        "hgf_aggregate_margin": (c_int, [vp, vp, vp, c_int, c_int, vp, vp, vp, vp]),
         "hgf_filter_host": (c_int, [vp, vp, c_int, c_int, c_int, P(hgf_params), vp, c_int, c_int,
                                     vp, vp, vp]),
         "hgf_set_tuning": (c_int, [vp, P(hgf_tuning)]),
@@ -289,6 +292,24 @@ def hgf_aggregate_plain(ctx, g, cost, filtered=None, labels=None, best=None, str
     _check(ctx, lib().hgf_aggregate_plain(ctx, g, _ptr(cost), _dtype_code(cost), L,
                                           _ptr(filtered), HGF_F32, _ptr(labels), _ptr(best),
                                           _stream(stream)))
+
+
+def hgf_aggregate_margin(ctx, g, cost, margin, labels=None, best=None, stream=None):
+    """hgf_aggregate with the WTA margin: second-smallest minus smallest filtered cost."""
+    for t, nm in ((cost, "cost"), (margin, "margin"), (labels, "labels"), (best, "best")):
+        _require_cuda(t, nm)
+    L = cost.shape[0]
+    _check(ctx, lib().hgf_aggregate_margin(ctx, g, _ptr(cost), _dtype_code(cost), L,
+                                           _ptr(labels), _ptr(best), _ptr(margin),
+                                           _stream(stream)))
+
+
+def hgf_wta_margin(ctx, filtered, margin, labels=None, best=None, stream=None):
+    for t, nm in ((filtered, "filtered"), (margin, "margin"), (labels, "labels"), (best, "best")):
+        _require_cuda(t, nm)
+    L, H, W = filtered.shape
+    _check(ctx, lib().hgf_wta_margin(ctx, _ptr(filtered), HGF_F32, L, H, W, _ptr(labels),
+                                     _ptr(best), _ptr(margin), _stream(stream)))
 
 
 def hgf_wta(ctx, filtered, labels=None, best=None, stream=None):
