@@ -141,9 +141,10 @@ hgf_status hgf_aggregate(hgf_ctx *ctx, const hgf_guidance *g, const void *cost, 
                          int L, void *filtered, int filtered_dtype, int32_t *labels, float *best,
                          void *stream);
 
-/* hgf_aggregate for callers that cannot allocate device memory while they run (work recorded into
- * a CUDA graph, fixed-latency loops, or programs whose device memory is handed out by their own
- * allocator at start-up): the same kernels and results, but the scratch - per-pixel WTA keys and
+/* hgf_aggregate for callers that cannot allocate device memory while they run: fixed-latency loops
+ * (cudaMalloc/cudaFree can synchronise the device and block), or plugins in a program that hands
+ * out all device memory from its own allocator at start-up, where a late cudaMalloc fails or
+ * fragments that pool. The same kernels and results, but the scratch - per-pixel WTA keys and
  * per-chunk coefficient planes - comes from one fixed 64 MiB file-scope device array instead of
  * the context's growable workspace. No cudaMalloc/cudaFree or allocating library call is made.
  * The paper has no counterpart; it is a property of this library only.

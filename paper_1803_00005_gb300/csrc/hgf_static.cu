@@ -1,7 +1,8 @@
 // hgf_aggregate_static: the fused aggregation + WTA of hgf_aggregate for callers that must not
-// allocate device memory once they are running - for example a caller that records its work
-// into a CUDA graph or runs a fixed-latency loop (cudaMalloc/cudaFree synchronise the device and
-// may block), or one whose memory is fully handed out by its own allocator at start-up. Instead of
+// allocate device memory once they are running - for example a fixed-latency loop (cudaMalloc and
+// cudaFree can synchronise the device and block for an unbounded time), or a plugin inside a host
+// program that hands out all device memory from its own allocator at start-up, so that a late
+// cudaMalloc fails or fragments the host's pool. Instead of
 // the context's growable workspace, this entry point takes its scratch (the per-pixel WTA keys and
 // the per-chunk coefficient planes) from one file-scope device array of fixed size, which every
 // GPU that loads this library holds until the process exits.

@@ -1,6 +1,7 @@
 """hgf_aggregate_static: the aggregation entry point for callers that must not allocate device
-memory while running (graph capture, fixed-latency loops, pre-partitioned memory). It takes its
-scratch from the library's fixed device array; this test checks, through the C ABI, that two calls
+memory while running (fixed-latency loops, where cudaMalloc can block; plugins in a program whose
+allocator owns all device memory from start-up). It takes its scratch from the library's fixed
+device array; this test checks, through the C ABI, that two calls
 in a row give what the allocating hgf_aggregate gives on the same inputs, and that an image too
 large for the array is refused with a clear error instead of being processed."""
 import numpy as np
