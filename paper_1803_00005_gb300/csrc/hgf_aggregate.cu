@@ -146,7 +146,7 @@ AggregatePlan plan_aggregate(const hgf_guidance *g, int L, const hgf_tuning &t, 
       ((t.labels_per_pass == 4 || t.labels_per_pass == 8) &&
        coef_smem(g->n, g->C, t.labels_per_pass, g->r) <= 227 * 1024))
     p.K = t.labels_per_pass;
-  const size_t plane = (size_t)coef_floats(g->n) * g->H * g->W * sizeof(float);
+  const size_t plane = coef_plane_floats(g->n, (size_t)g->H * g->W) * sizeof(float);
   // labels per chunk: all labels while the coefficient workspace stays under 4 GiB
   size_t cap = std::max<size_t>(1, ((size_t)4 << 30) / plane);
   p.chunk = t.chunk_labels > 0 ? t.chunk_labels : (int)std::min<size_t>((size_t)L, cap);
@@ -166,7 +166,7 @@ AggregatePlan plan_aggregate(const hgf_guidance *g, int L, const hgf_tuning &t, 
 }
 
 size_t aggregate_coef_bytes(const hgf_guidance *g, const AggregatePlan &p) {
-  return (size_t)p.chunk * coef_floats(g->n) * g->H * g->W * sizeof(float);
+  return (size_t)p.chunk * coef_plane_floats(g->n, (size_t)g->H * g->W) * sizeof(float);
 }
 
 cudaError_t launch_aggregate(const hgf_guidance *g, const void *cost, int cost_dtype, int L,

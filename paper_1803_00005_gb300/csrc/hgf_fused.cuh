@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(NT, (coef_min_blocks<B, K, COMP>())) k_coef(co
   __shared__ int s_fail;
   const int R = 2 * r + 1;
   const size_t HW = (size_t)H * W;
+  const size_t plane = coef_plane_floats(NG, HW);  // floats per label in the coefficient workspace
   // grid: x = label pass (fastest, so every pass over one strip and band runs back to back and
   // they share the strip's inverse records through L2), y = strip, z = band
   const int t = threadIdx.x;
@@ -321,10 +322,10 @@ __global__ void __launch_bounds__(NT, (coef_min_blocks<B, K, COMP>())) k_coef(co
               for (int i = 0; i < C1; ++i) o[i] = v[kk][i];
 #pragma unroll
               for (int i = C1; i < CP; ++i) o[i] = 0.f;
-              float2 *dst =
-                  reinterpret_cast<float2 *>(coef + ((size_t)(k0 + kb + kk) * HW + pix) * CP);
+              float2 *dst = reinterpret_cast<float2 *>(coef + (size_t)(k0 + kb + kk) * plane) +
+                            coef_pair_index(NG, pix, 0);
 #pragma unroll
-              for (int q = 0; q < CP / 2; ++q) dst[q] = make_float2(o[2 * q], o[2 * q + 1]);
+              for (int q = 0; q < CP / 2; ++q) dst[q * 32] = make_float2(o[2 * q], o[2 * q + 1]);
             }
           }
         }
@@ -376,10 +377,10 @@ __global__ void __launch_bounds__(NT, (coef_min_blocks<B, K, COMP>())) k_coef(co
             for (int i = 0; i < NG; ++i) o[i + 1] = a[kk][i];
 #pragma unroll
             for (int i = C1; i < CP; ++i) o[i] = 0.f;
-            float2 *dst =
-                reinterpret_cast<float2 *>(coef + ((size_t)(k0 + kb + kk) * HW + pix) * CP);
+            float2 *dst = reinterpret_cast<float2 *>(coef + (size_t)(k0 + kb + kk) * plane) +
+                          coef_pair_index(NG, pix, 0);
 #pragma unroll
-            for (int q = 0; q < CP / 2; ++q) dst[q] = make_float2(o[2 * q], o[2 * q + 1]);
+            for (int q = 0; q < CP / 2; ++q) dst[q * 32] = make_float2(o[2 * q], o[2 * q + 1]);
           }
         }
       }
@@ -432,13 +433,14 @@ __global__ void __launch_bounds__(NT) k_apply(const float *__restrict__ coef, in
   float sh[NG];
 #pragma unroll
   for (int i = 0; i < NG; ++i) sh[i] = __ldg(shift + i);
-  const float *cb = coef + (size_t)k * HW * CP;
+  const float *cb = coef + (size_t)k * coef_plane_floats(NG, HW);
   auto load_row = [&](int row, float *v) {
     if (col_ok && row >= 0 && row < H) {
-      const float2 *src = reinterpret_cast<const float2 *>(cb + ((size_t)row * W + xc) * CP);
+      const float2 *src =
+          reinterpret_cast<const float2 *>(cb) + coef_pair_index(NG, (size_t)row * W + xc, 0);
 #pragma unroll
       for (int q = 0; q < CP / 2; ++q) {
-        const float2 u = __ldg(src + q);
+        const float2 u = __ldg(src + q * 32);
         if (2 * q < C1) v[2 * q] = u.x;
         if (2 * q + 1 < C1) v[2 * q + 1] = u.y;
       }

@@ -77,6 +77,19 @@ __host__ __device__ constexpr bool coef_reload(int n) {
 // Per-pixel coefficient record of the fused kernels' workspace: [b, a_1..a_n | padding] rounded
 // up to an even count so that it is read and written as float2 pairs.
 __host__ __device__ constexpr int coef_floats(int n) { return (n + 1 + 1) / 2 * 2; }
+// The workspace holds one plane per label of the chunk. A plane is tiled by 32 consecutive pixels
+// of the flattened index p = y * W + x: tile p / 32 is coef_floats(n) / 2 runs of 32 float2, run q
+// holding pair q of the tile's 32 records (coef_pair_index). A warp's 32 consecutive pixels then
+// touch at most two tiles, so each float2 access of the warp is one or two contiguous runs
+// instead of 32 records 4 * coef_floats(n) bytes apart, and a strip's row stays one contiguous
+// block as in a pixel-major layout. The plane is padded to a whole number of tiles.
+__host__ __device__ constexpr size_t coef_plane_floats(int n, size_t HW) {
+  return (HW + 31) / 32 * 32 * (size_t)coef_floats(n);
+}
+// Index, in float2 units from the start of a plane, of pair q of pixel p's record.
+__host__ __device__ __forceinline__ size_t coef_pair_index(int n, size_t p, int q) {
+  return (p >> 5) * (size_t)(coef_floats(n) / 2) * 32 + (size_t)q * 32 + (p & 31);
+}
 
 // Packed upper-triangle index of (i, j), i <= j, row by row.
 __host__ __device__ constexpr int tri_index(int n, int i, int j) {

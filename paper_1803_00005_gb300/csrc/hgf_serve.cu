@@ -212,7 +212,7 @@ struct hgf_server {
     if (err == cudaSuccess) {
       hgf_tuning t = sl.ctx->tuning;
       AggregatePlan plan = plan_aggregate(&e->g, r.L, t, num_sms);
-      const size_t per_label = (size_t)coef_floats(q->n) * r.H * r.W * sizeof(float);
+      const size_t per_label = coef_plane_floats(q->n, (size_t)r.H * r.W) * sizeof(float);
       plan.chunk = std::max(1, std::min(plan.chunk, (int)(sl.ctx->ws_coef.size / per_label)));
       err = launch_aggregate(&e->g, r.cost, r.cost_dtype, r.L, nullptr, r.labels, r.best,
                              (float *)sl.ctx->ws_coef.ptr,
@@ -318,7 +318,7 @@ hgf_status hgf_serve_create(int device, size_t budget_bytes, int slots, int max_
   // coefficient records at n = max_n (fewer labels per chunk are used when a request is bigger),
   // and the WTA keys
   const size_t prep = prepare_workspace_bytes(max_n, 1, max_pixels);
-  const size_t coef = (size_t)16 * coef_floats(max_n) * max_pixels * sizeof(float);
+  const size_t coef = (size_t)16 * coef_plane_floats(max_n, (size_t)max_pixels) * sizeof(float);
   const size_t keys = (size_t)max_pixels * sizeof(unsigned long long);
   s->slot_bytes = (size_t)slots * (prep + coef + keys);
   if (s->slot_bytes > budget_bytes) return cleanup(HGF_ENOMEM);

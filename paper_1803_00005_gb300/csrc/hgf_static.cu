@@ -75,7 +75,7 @@ extern "C" hgf_status hgf_aggregate_static(hgf_ctx *ctx, const hgf_guidance *g, 
   hgf::AggregatePlan plan = hgf::plan_aggregate(g, L, ctx->tuning, ctx->num_sms);
   const size_t HW = (size_t)g->H * g->W;
   const size_t keys_bytes = (HW * sizeof(unsigned long long) + 255) / 256 * 256;
-  const size_t per_label = (size_t)hgf::coef_floats(g->n) * HW * sizeof(float);
+  const size_t per_label = hgf::coef_plane_floats(g->n, HW) * sizeof(float);
   if (keys_bytes + per_label > kStaticScratchBytes)
     return fail(HGF_EUNSUPPORTED,
                 "image too large for the " + std::to_string(kStaticScratchBytes >> 20) +
