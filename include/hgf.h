@@ -152,7 +152,7 @@ hgf_status hgf_aggregate(hgf_ctx *ctx, const hgf_guidance *g, const void *cost, 
  * on a device looks up its address (cudaGetSymbolAddress) with that device current: make it before
  * any stream capture. All calls share the array and it keeps the last call's contents (the keys
  * are reset by every call); calls that overlap on the GPU race and must be serialised. Returns
- * HGF_EUNSUPPORTED when one label's coefficient planes plus the keys exceed 64 MiB (about 1.3
+ * HGF_EUNSUPPORTED when one label's coefficient planes plus the keys exceed 64 MiB (about 1.4
  * Mpixel at n = 9), or when the window is too wide for the fused kernels. Same arguments as
  * hgf_aggregate. */
 hgf_status hgf_aggregate_static(hgf_ctx *ctx, const hgf_guidance *g, const void *cost,
