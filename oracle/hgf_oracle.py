@@ -40,7 +40,7 @@ import numpy as np
 __all__ = [
     "box_sum", "window_count", "box_mean", "monomial_exponents", "polynomial_guidance",
     "n_channels", "cholesky_solve", "hgf_alpha", "hgf_inverse", "guidance_moments",
-    "centred_filter", "centred_filter_hgf", "paper_filter", "wta", "filter_at",
+    "centred_filter", "centred_filter_hgf", "paper_filter", "wta", "filter_at", "filter_region",
 ]
 
 
@@ -367,3 +367,17 @@ def filter_at(I, P, r, eps, degree, points, basis="monomial"):
                            r, eps, degree, basis)
         out[:, t] = q[:, y - y0, x - x0]
     return out
+
+
+def filter_region(I, P, r, eps, degree, y0, y1, x0, x1, basis="monomial"):
+    """Form A output on the rectangle [y0, y1) x [x0, x1) of a large image, computed, as in
+    filter_at, on the smallest crop that holds every input it depends on (the rectangle grown by
+    2r on each side and clipped to the image): exact, because windows that touch the image border
+    are clipped by the same border inside the crop. Returns (K, y1 - y0, x1 - x0)."""
+    P = np.asarray(P)
+    H, W = P.shape[-2:]
+    cy0, cy1 = max(0, y0 - 2 * r), min(H, y1 + 2 * r)
+    cx0, cx1 = max(0, x0 - 2 * r), min(W, x1 + 2 * r)
+    q = centred_filter(np.asarray(I)[:, cy0:cy1, cx0:cx1],
+                       np.asarray(P[:, cy0:cy1, cx0:cx1], dtype=np.float64), r, eps, degree, basis)
+    return q[:, y0 - cy0:y1 - cy0, x0 - cx0:x1 - cx0]

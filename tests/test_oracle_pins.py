@@ -361,6 +361,20 @@ def test_filter_at_matches_full_image():
         np.testing.assert_allclose(got[:, t], q[:, y, x], rtol=1e-12, atol=1e-15)
 
 
+def test_filter_region_matches_full_image():
+    """filter_region on rectangles at the corners, the edges and the interior (and one wider than
+    the crop margin) equals the full-image filter there."""
+    H, W, r = 31, 37, 3
+    g = rng(12)
+    I = g.uniform(size=(3, H, W)).astype(np.float32)
+    P = (g.uniform(size=(3, H, W)) * 0.03).astype(np.float32)
+    q = O.centred_filter(I, P, r, 1e-4, 2)
+    for y0, y1, x0, x1 in ((0, 5, 0, 4), (26, 31, 30, 37), (10, 17, 12, 25), (0, 31, 35, 37),
+                           (3, 4, 0, 37)):
+        got = O.filter_region(I, P, r, 1e-4, 2, y0, y1, x0, x1)
+        np.testing.assert_allclose(got, q[:, y0:y1, x0:x1], rtol=1e-12, atol=1e-15)
+
+
 # ------------------------------------------------------------------------------- cost volume
 def test_cost_volume_zero_at_the_true_shift():
     """A scene point at left x seen at right x - d (right(x') = left(x' + d)): the
