@@ -43,6 +43,8 @@ FP64_PEAK_TFLOPS = 1.25                              # nominal GB300 FP64 rate
 def flops_per_unit(kernel: str, n: int) -> tuple[float, str] | None:
     """Algorithmic flops per unit (pixel*label for the aggregation kernels, pixel for the
     inverse) and the unit name."""
+    if kernel == "k_fused":     # the whole per-label path: both box stages, cov, mat-vec,
+        return 2 * n * n + 17 * n + 10, "px*label"   # offset, output and the WTA compare
     if kernel == "k_coef":      # n products, 5(n+1) box, 2n cov, 2n^2 mat-vec, 2n offset
         return 2 * n * n + 10 * n + 5, "px*label"
     if kernel == "k_apply":     # 5(n+1) box, 2n output, 1 compare
@@ -94,6 +96,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["fused", "plain", "reference"], default="fused")
     ap.add_argument("--workload", choices=list(WORKLOADS), default="quarter")
+    ap.add_argument("--kernel", type=int, choices=[0, 1, 2], default=0,
+                    help="fused path: 0 automatic, 1 single-pass kernel, 2 two kernels")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--inv-precision", choices=["f64", "df64", "f32"], default="f64",
                     help="arithmetic of the covariance assembly + inverse")
@@ -589,6 +593,8 @@ def main():
                              inv_precision=args.inv_precision)
     g = hgf.hgf_prepare(ctx, img, params)
     agg = hgf.hgf_aggregate_plain if args.impl == "plain" else hgf.hgf_aggregate
+    if args.kernel:
+        hgf.hgf_set_tuning(ctx, kernel=args.kernel)
 
     def step():
         hgf.hgf_guidance_update(ctx, g, img)

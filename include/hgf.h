@@ -130,7 +130,9 @@ hgf_status hgf_guidance_export(hgf_ctx *ctx, const hgf_guidance *g, float *minv_
 /* Fused aggregation + WTA (Sec. 1 pipeline; Eqs. GF_w / HGF_z1): for every label slice p of the
  * cost volume, pbar = A(p), cov_i = A(G_i p) - mu_i pbar, a = (Sigma + eps E)^-1 cov,
  * b = pbar - a.mu, q = sum_i A(a_i) G_i + A(b); then labels = argmin_l q_l (lowest l on ties,
- * NaN counted as +inf) and best = min_l q_l. For a guidance prepared with HGF_FORM_PAPER the
+ * NaN counted as +inf) and best = min_l q_l. By default two kernels per chunk of labels with a
+ * coefficient workspace in between; for n <= 9 (r <= 24) hgf_tuning.kernel = 1 selects one
+ * kernel that does all of it, WTA included, in a single pass over the slices. For a guidance prepared with HGF_FORM_PAPER the
  * coefficients are those of the paper's form instead: w = (lambda E + Gram)^-1 B([1, G] p) and
  * q = sum_i A(w_i) G_i + A(w_0) (see hgf_form).
  * cost: device, L x H x W of cost_dtype (HGF_F32, HGF_BF16 or HGF_F16), H, W of the guidance.
@@ -145,16 +147,22 @@ hgf_status hgf_aggregate(hgf_ctx *ctx, const hgf_guidance *g, const void *cost, 
  * (cudaMalloc/cudaFree can synchronise the device and block), or plugins in a program that hands
  * out all device memory from its own allocator at start-up, where a late cudaMalloc fails or
  * fragments that pool. The same kernels and results, but the scratch - per-pixel WTA keys and
- * per-chunk coefficient planes - comes from one fixed 64 MiB file-scope device array instead of
- * the context's growable workspace. No cudaMalloc/cudaFree or allocating library call is made.
+ * either per-chunk coefficient planes (two-kernel path, the default) or the single-pass kernel's
+ * ring slots (hgf_tuning.kernel = 1) - comes from one fixed 64 MiB file-scope device array
+ * instead of the context's growable workspace. No cudaMalloc/cudaFree or allocating library call
+ * is made.
  * The paper has no counterpart; it is a property of this library only.
- * The array is held by every GPU that loads the library until the process exits. The first call
- * on a device looks up its address (cudaGetSymbolAddress) with that device current: make it before
- * any stream capture. All calls share the array and it keeps the last call's contents (the keys
- * are reset by every call); calls that overlap on the GPU race and must be serialised. Returns
- * HGF_EUNSUPPORTED when one label's coefficient planes plus the keys exceed 64 MiB (about 1.4
- * Mpixel at n = 9), or when the window is too wide for the fused kernels. Same arguments as
- * hgf_aggregate. */
+ * The array is held by every GPU that loads the library until the process exits. hgf_create
+ * commits it on the context's device and looks up its address (cudaGetSymbolAddress) with that
+ * device current; if that failed (no memory left), the first call here tries again, returns
+ * HGF_ENOMEM while it fails (the context stays usable), and should then come before any stream
+ * capture. All calls share the array and it keeps the last call's contents (the keys are reset by
+ * every call, every coefficient plane is written before it is read); calls that overlap on the
+ * GPU race and must be serialised. Returns HGF_EUNSUPPORTED when the keys (8 bytes a pixel) plus
+ * one label's coefficient planes (two-kernel path: about 1.4 Mpixel at n = 9) or plus one ring
+ * slot (single pass: 140 KB at n = 9, r = 9; about 8 Mpixel) exceed 64 MiB, or when the window is
+ * too wide for the fused kernels.
+ * Same arguments as hgf_aggregate. */
 hgf_status hgf_aggregate_static(hgf_ctx *ctx, const hgf_guidance *g, const void *cost,
                                 int cost_dtype, int L, void *filtered, int filtered_dtype,
                                 int32_t *labels, float *best, void *stream);
@@ -199,23 +207,34 @@ hgf_status hgf_filter_host(hgf_ctx *ctx, const float *img, int C, int H, int W,
                            int32_t *labels, float *best, void *stream);
 
 /* Tuning of the fused kernels (0 = automatic): labels per pass of the coefficient kernel (2, 4, 8),
- * row-band height, labels per chunk of the coefficient workspace, and how the output kernel gets
- * the row leaving its vertical window (1 = shared-memory ring, 2 = reload from device memory).
- * Returns HGF_EINVAL for values the kernels cannot take. */
+ * row-band height, labels per chunk of the coefficient workspace, how the output kernel gets
+ * the row leaving its vertical window (1 = shared-memory ring, 2 = reload from device memory),
+ * and which kernels run: kernel = 1 the single-pass kernel (slice moments, coefficients, their
+ * box filter, output and WTA of two labels at a time in one pass over the slices, with a small
+ * L2-resident ring of coefficient window sums instead of a coefficient workspace; n <= 9 and
+ * r <= 24), 2 (or 0, automatic) the two-kernel path (coefficients to a workspace, then output +
+ * WTA: the only one for n = 19). labels_per_pass, chunk_labels and apply_mode apply to
+ * the two-kernel path only. Returns HGF_EINVAL for values the kernels cannot take. */
 typedef struct {
   int labels_per_pass;
   int band_rows;
   int chunk_labels;
   int apply_mode;
+  int kernel;
 } hgf_tuning;
 hgf_status hgf_set_tuning(hgf_ctx *ctx, const hgf_tuning *t);
-/* Autotuner (no counterpart in the paper): times hgf_aggregate on (g, cost) under every tuning
- * that leaves the results bit-identical - labels per pass 2, 4 or 8 (where shared memory allows),
- * labels per chunk (all, 64, 16) and the output kernel's outgoing-row source (reload, ring) -
- * with the row bands of the automatic plan (bands change rounding, so they are not tuned). Each
- * candidate runs once untimed, then `reps` times between CUDA events on `stream`. The fastest
- * becomes ctx's tuning and is written to *best (may be NULL); *ncand (may be NULL) receives the
- * number of candidates timed. labels: device int32 H x W, scratch output. Blocks until done.
+/* Autotuner (no counterpart in the paper): times hgf_aggregate on (g, cost) under every candidate
+ * tuning - first the kernel path (single pass where it applies, two kernels with labels per pass
+ * 2, 4 or 8 where shared memory allows, labels per chunk all / 64 / 16 and the output kernel's
+ * outgoing-row source), with the automatic row bands; then, for the fastest of those, row-band
+ * heights of a half, a quarter and an eighth of the image - and makes the fastest ctx's tuning.
+ * Candidates of the two-kernel family with the same bands give bit-identical results; the
+ * path and the band height change only the order of the sums' rounding (every candidate is
+ * within the filter's tolerance). Keep one tuning per shape class (bench.py and hgf.py's
+ * autotune_cached key it by GPU, n, r, cost dtype and size class), so that alone, batched and
+ * served runs of a shape use one plan. Each candidate runs once untimed, then `reps` times
+ * between CUDA events on `stream`; *best (may be NULL) receives the pick, *ncand (may be NULL)
+ * the number of candidates timed. labels: device int32 H x W, scratch output. Blocks until done.
  * HGF_EINVAL on bad arguments or reps < 1; errors of hgf_aggregate otherwise. */
 hgf_status hgf_autotune(hgf_ctx *ctx, const hgf_guidance *g, const void *cost, int cost_dtype,
                         int L, int32_t *labels, int reps, hgf_tuning *best, int *ncand,
@@ -390,6 +409,14 @@ hgf_status hgf_batched_inverse(hgf_ctx *ctx, const double *S, int count, int n, 
  * CUDA event pair on its stream. hgf_profile_report: waits for the recorded events, writes
  * {"kernel": {"launches": n, "ms": total}, ...} as JSON into buf (cap bytes) and clears them. */
 hgf_status hgf_launch_count(hgf_ctx *ctx, unsigned long long *out);
+/* The plan of ctx's last aggregation (no counterpart in the paper), for tests and tuning: writes
+ * n ints (n >= 1; entries past the eighth are 0) to out: [0] path (1 single-pass kernel, 2 two
+ * kernels, 3 plain form, 0 none yet), [1] output columns per strip (strip s covers columns
+ * [s * out[1], (s + 1) * out[1])), [2] coefficient columns per strip, [3] rows per band of the
+ * coefficient (or single-pass) kernel, [4] rows per band of the output kernel (bands start at
+ * multiples of these), [5] labels per pass, [6] labels per chunk (of the last chunk launched),
+ * [7] CTAs of the last launch. HGF_EINVAL for NULL arguments or n < 1. */
+hgf_status hgf_last_plan(hgf_ctx *ctx, int *out, int n);
 /* Kernel watchdog (no counterpart in the paper). Every wait inside a kernel (for a bulk copy into
  * shared memory) is bounded; a wait that runs out sets a per-device status word, the kernel stops
  * its CTA early and that call's results are incomplete. hgf_device_status waits for all work on

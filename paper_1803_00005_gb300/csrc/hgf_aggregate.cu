@@ -4,6 +4,8 @@
 #include "hgf_basis.cuh"
 #include "hgf_mbarrier.cuh"
 
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <mutex>
 
@@ -78,14 +80,69 @@ __global__ void k_watchdog_probe(int *status, unsigned long long limit_ns) {
 }  // namespace
 
 // Dynamic shared memory of k_coef for n guidance channels, C input channels, K labels, radius r:
-// two mbarriers, two scan buffers, two staged record blocks, the raw-row ring (ring mode only).
+// 128 bytes of alignment slack, the staged record boxes, two mbarriers, two scan buffers, the
+// raw-row ring (ring mode only).
 size_t coef_smem(int n, int C, int K, int r) {
-  const bool stage = records_strip_tiled(n);
-  return 16 + sizeof(float) * ((size_t)2 * K * (n + 1) * kRowStride +
-                               (stage ? (size_t)kRecordBuffers * record_floats(n) *
-                                            (NT - 2 * r)
-                                      : 0) +
-                               (coef_reload(n) ? 0 : (size_t)(2 * r + 1) * (C + K) * NT));
+  const bool stage = records_staged(n);
+  const size_t rbuf = ((size_t)record_floats(n) * record_box_width(r) + 31) / 32 * 32;
+  return 128 + 16 +
+         sizeof(float) * ((size_t)2 * K * (n + 1) * kRowStride +
+                          (stage ? (size_t)kRecordBuffers * rbuf : 0) +
+                          (coef_reload(n) ? 0 : (size_t)(2 * r + 1) * (C + K) * NT));
+}
+
+// Dynamic shared memory of the single-pass kernel k_fused (hgf_onepass.cuh): 128 bytes of
+// alignment slack, the record box, an mbarrier and the scan rows of both stages for its labels.
+size_t onepass_smem(int n, int r) {
+  (void)r;
+  return 128 + sizeof(float) * (size_t)record_floats(n) * kFusedBoxWidth + 16 +
+         sizeof(float) * (size_t)2 * kFusedLabels * (n + 1) * kRowStride;
+}
+
+// Its ring buffer: per CTA, (2r+1) rows x labels x (n + 1) channels x (128 - 4r) output columns.
+size_t onepass_ring_bytes(int n, int r, int ctas) {
+  return sizeof(float) * (size_t)ctas * (2 * r + 1) * kFusedLabels * (n + 1) * (NT - 4 * r);
+}
+
+// The single-pass kernel serves n <= 9 (records staged) while its strip keeps at least 32 output
+// columns (r <= 24) and its shared memory fits one CTA.
+bool onepass_fits(const hgf_guidance *g) {
+  return records_staged(g->n) && NT - 4 * g->r >= 32 && onepass_smem(g->n, g->r) <= 227 * 1024;
+}
+
+// Tensor map of the plane-major records of g: dims (W, H, REC) with row pitch record_pitch(W),
+// box (record_box_width(r), 1, REC); columns outside [0, W) load as zeros. The encoder is the
+// driver's cuTensorMapEncodeTiled, looked up once through the runtime.
+cudaError_t make_record_map(const hgf_guidance *g, CUtensorMap *out, int box_w) {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  std::call_once(once, [] {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    else
+      cudaGetLastError();
+  });
+  if (!encode) {
+    note_failed("cuTensorMapEncodeTiled lookup");
+    return cudaErrorNotSupported;
+  }
+  const int REC = record_floats(g->n);
+  const cuuint64_t P = (cuuint64_t)record_pitch(g->W);
+  const cuuint64_t dims[3] = {(cuuint64_t)g->W, (cuuint64_t)g->H, (cuuint64_t)REC};
+  const cuuint64_t strides[2] = {P * sizeof(float), P * g->H * sizeof(float)};
+  const int bw = box_w > 0 ? box_w : record_box_width(g->r);
+  const cuuint32_t box[3] = {(cuuint32_t)bw, 1u, (cuuint32_t)REC};
+  const cuuint32_t estr[3] = {1u, 1u, 1u};
+  if (REC > 256 || bw > 256 || bw % 4) return cudaErrorInvalidValue;
+  CUresult r = encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)g->rec, dims, strides, box,
+                      estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) note_failed("cuTensorMapEncodeTiled");
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 // Device address of the watchdog word on the current device (looked up once per device).
@@ -162,10 +219,17 @@ AggregatePlan plan_aggregate(const hgf_guidance *g, int L, const hgf_tuning &t, 
   (void)passes;
   (void)num_sms;
   p.band_rows = t.band_rows;  // 0: each kernel picks its bands from its occupancy at launch
+  // the two-kernel path unless tuned to the single-pass kernel (within its range): measured on
+  // GB300 the two are level at 450x375 / L = 60 / n = 9 / r = 9 (0.54 ms each) and the two-kernel
+  // path is ahead at 1400x1100 / L = 256 (18.0 vs 21.4 ms), where the single pass's narrower
+  // output strips (128 - 4r columns against 128 - 2r) cost more than its saved workspace traffic
+  p.onepass = t.kernel == 1 && onepass_fits(g);
+  p.onepass_ctas = std::max(1, num_sms) * kFusedCtasPerSm;
   return p;
 }
 
 size_t aggregate_coef_bytes(const hgf_guidance *g, const AggregatePlan &p) {
+  if (p.onepass) return onepass_ring_bytes(g->n, g->r, p.onepass_ctas);
   return (size_t)p.chunk * coef_plane_floats(g->n, (size_t)g->H * g->W) * sizeof(float);
 }
 
@@ -188,11 +252,14 @@ cudaError_t launch_aggregate(const hgf_guidance *g, const void *cost, int cost_d
   const int b = basis_id(g->C, g->degree, g->basis);
   int *status = device_status_ptr();
   if (!status) return cudaErrorInvalidValue;
-  cudaError_t e = cudaErrorInvalidValue;
+  CUtensorMap map;
+  cudaError_t e = make_record_map(g, &map, p.onepass ? kFusedBoxWidth : 0);
+  if (e != cudaSuccess) return e;
+  e = cudaErrorInvalidValue;
   bool ok = dispatch_basis(b, [&](auto bc) {
     constexpr int B = decltype(bc)::value;
     e = launch_basis<B>(g, cost, cost_dtype, L, filtered, coef_ws, k, p, status,
-                        stereo ? *stereo : StereoSource{}, s, prof);
+                        stereo ? *stereo : StereoSource{}, map, s, prof);
   });
   if (!ok) return cudaErrorInvalidValue;
   if (e != cudaSuccess) return e;

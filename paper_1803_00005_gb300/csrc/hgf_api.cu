@@ -26,9 +26,18 @@ hgf_status set_err(hgf_ctx *ctx, hgf_status st, const char *fmt, ...) {
   return st;
 }
 
+// " in <step>" for the launch or set-up call that failed (failed_step), consumed here.
+std::string failed_suffix() {
+  const char *st = failed_step();
+  failed_step() = nullptr;
+  return st ? std::string(" in ") + st : std::string();
+}
+
 hgf_status cuda_fail(hgf_ctx *ctx, cudaError_t e, const char *where) {
   ctx->sticky.store(HGF_ECUDA);
-  return set_err(ctx, HGF_ECUDA, "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
+  const std::string in = failed_suffix();
+  return set_err(ctx, HGF_ECUDA, "%s: %s (%s)%s", where, cudaGetErrorName(e),
+                 cudaGetErrorString(e), in.c_str());
 }
 
 // Enters an API call on ctx: refuses work after a CUDA failure and makes the device current.
@@ -80,7 +89,8 @@ hgf_status grow(hgf_ctx *ctx, Workspace &w, size_t bytes, cudaStream_t s) {
 // CUDA failure with ctx->mu held.
 hgf_status cuda_fail_locked(hgf_ctx *ctx, cudaError_t e, const char *where) {
   ctx->sticky.store(HGF_ECUDA);
-  ctx->err = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  ctx->err = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")" +
+             failed_suffix();
   return HGF_ECUDA;
 }
 
@@ -138,7 +148,7 @@ hgf_status alloc_guidance(hgf_ctx *ctx, int C, int H, int W, int n, const hgf_pa
   g->form = p->form;
   g->compensated = p->compensated;
   const size_t HW = (size_t)H * W;
-  const size_t rec_floats = record_total_floats(H, W, n, g->r);
+  const size_t rec_floats = record_total_floats(H, W, n);
   const size_t floats = HW * ((size_t)C + n + packed_size(n) + n) + rec_floats + 64;
   float *base = nullptr;
   cudaError_t e = cudaMalloc(&base, floats * sizeof(float));
@@ -148,7 +158,7 @@ hgf_status alloc_guidance(hgf_ctx *ctx, int C, int H, int W, int n, const hgf_pa
     return set_err(ctx, HGF_ENOMEM, "cannot allocate %zu bytes for the guidance",
                    floats * sizeof(float));
   }
-  g->rec = base;  // first: bulk copies of record blocks need the allocation's alignment
+  g->rec = base;  // first: tensor copies of record rows need the allocation's alignment
   g->img = g->rec + rec_floats;
   g->G = g->img + (size_t)C * HW;
   g->minv = g->G + (size_t)n * HW;
@@ -265,6 +275,9 @@ hgf_status hgf_create(int device, hgf_ctx **out) {
   if (!ctx) return HGF_ENOMEM;
   ctx->device = device;
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  // commit hgf_aggregate_static's fixed scratch now, while the caller expects allocations; if it
+  // fails (no memory left), that entry point retries and reports HGF_ENOMEM
+  if (static_scratch_init(device) != cudaSuccess) cudaGetLastError();
   *out = ctx;
   return HGF_OK;
 }
@@ -384,6 +397,7 @@ hgf_status hgf_set_tuning(hgf_ctx *ctx, const hgf_tuning *t) {
     return set_err(ctx, HGF_EINVAL, "band_rows and chunk_labels must be >= 0");
   if (t->apply_mode < 0 || t->apply_mode > 2)
     return set_err(ctx, HGF_EINVAL, "apply_mode must be 0, 1 or 2");
+  if (t->kernel < 0 || t->kernel > 2) return set_err(ctx, HGF_EINVAL, "kernel must be 0, 1 or 2");
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   ctx->tuning = *t;
   return HGF_OK;
@@ -400,36 +414,55 @@ hgf_status hgf_autotune(hgf_ctx *ctx, const hgf_guidance *g, const void *cost, i
   if (!labels || reps < 1) return set_err(ctx, HGF_EINVAL, "labels is NULL or reps < 1");
   cudaStream_t s = (cudaStream_t)stream;
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  // first round: the kernel path and the two-kernel path's labels per pass, chunk and ring
+  // mode, all with the automatic row bands
   std::vector<hgf_tuning> cands;
   for (int K : {2, 4, 8}) {
     if (K != 2 && coef_smem(g->n, g->C, K, g->r) > 227 * 1024) continue;
     for (int chunk : {0, 64, 16}) {
       if (chunk != 0 && chunk >= L) continue;
-      for (int apply : {2, 1}) cands.push_back(hgf_tuning{K, 0, chunk, apply});
+      for (int apply : {2, 1}) cands.push_back(hgf_tuning{K, 0, chunk, apply, 2});
     }
   }
+  if (onepass_fits(g)) cands.push_back(hgf_tuning{0, 0, 0, 0, 1});
   cudaEvent_t a = nullptr, b = nullptr;
   cudaError_t e = cudaEventCreate(&a);
   if (e == cudaSuccess) e = cudaEventCreate(&b);
   const hgf_tuning saved = ctx->tuning;
   float best_ms = 0.f;
   hgf_tuning pick = cands.front();
-  for (size_t i = 0; i < cands.size() && e == cudaSuccess && st == HGF_OK; ++i) {
-    ctx->tuning = cands[i];
-    st = aggregate_locked(ctx, g, cost, cost_dtype, L, nullptr, labels, nullptr, s);
-    if (st != HGF_OK) break;
-    e = cudaEventRecord(a, s);
-    for (int k = 0; k < reps && e == cudaSuccess && st == HGF_OK; ++k)
+  int timed = 0;
+  auto time_all = [&](const std::vector<hgf_tuning> &list) {
+    for (size_t i = 0; i < list.size() && e == cudaSuccess && st == HGF_OK; ++i) {
+      ctx->tuning = list[i];
       st = aggregate_locked(ctx, g, cost, cost_dtype, L, nullptr, labels, nullptr, s);
-    if (e == cudaSuccess) e = cudaEventRecord(b, s);
-    if (e == cudaSuccess) e = cudaEventSynchronize(b);
-    float ms = 0.f;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
-    if (e == cudaSuccess && (i == 0 || ms < best_ms)) {
-      best_ms = ms;
-      pick = cands[i];
+      if (st != HGF_OK) break;
+      e = cudaEventRecord(a, s);
+      for (int k = 0; k < reps && e == cudaSuccess && st == HGF_OK; ++k)
+        st = aggregate_locked(ctx, g, cost, cost_dtype, L, nullptr, labels, nullptr, s);
+      if (e == cudaSuccess) e = cudaEventRecord(b, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(b);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+      if (e == cudaSuccess && (timed == 0 || ms < best_ms)) {
+        best_ms = ms;
+        pick = list[i];
+      }
+      ++timed;
     }
+  };
+  time_all(cands);
+  // second round: row-band heights (tile shape along y) for the winner: a half, a quarter and an
+  // eighth of the image height, at least 4r + 8 rows (bands shorter than their warm-up waste it)
+  std::vector<hgf_tuning> bands;
+  for (int div : {2, 4, 8}) {
+    const int rows = (g->H + div - 1) / div;
+    if (rows < 4 * g->r + 8 || rows >= g->H) continue;
+    hgf_tuning t = pick;
+    t.band_rows = rows;
+    bands.push_back(t);
   }
+  time_all(bands);
   if (a) cudaEventDestroy(a);
   if (b) cudaEventDestroy(b);
   if (st != HGF_OK || e != cudaSuccess) {
@@ -438,7 +471,7 @@ hgf_status hgf_autotune(hgf_ctx *ctx, const hgf_guidance *g, const void *cost, i
   }
   ctx->tuning = pick;
   if (best) *best = pick;
-  if (ncand) *ncand = (int)cands.size();
+  if (ncand) *ncand = timed;
   return HGF_OK;
 }
 
@@ -847,6 +880,13 @@ hgf_status hgf_profile_enable(hgf_ctx *ctx, int enable) {
   if (!ctx) return HGF_EINVAL;
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   ctx->prof.enabled = enable != 0;
+  return HGF_OK;
+}
+
+hgf_status hgf_last_plan(hgf_ctx *ctx, int *out, int n) {
+  if (!ctx || !out || n < 1) return HGF_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  for (int i = 0; i < n; ++i) out[i] = i < 8 ? ctx->prof.plan[i] : 0;
   return HGF_OK;
 }
 

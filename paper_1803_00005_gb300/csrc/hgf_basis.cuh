@@ -65,6 +65,10 @@ __device__ __forceinline__ void eval_basis(const float *x, const float *shift, f
   }
 }
 
+// Bases for which the single-pass kernel (hgf_onepass.cuh) is built: n <= 9, whose records are
+// staged in shared memory.
+__host__ __device__ constexpr bool onepass_built(int b) { return basis_n(b) <= 9; }
+
 // Maps (C, degree, basis) to a basis id, -1 if not built.
 inline int basis_id(int C, int degree, int basis) {
   if (C == 1) return degree >= 1 && degree <= 9 ? B_GRAY1 + degree - 1 : -1;

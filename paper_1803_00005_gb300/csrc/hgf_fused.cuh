@@ -44,10 +44,11 @@ using strip::window;
 // bulk asynchronous copies and bounded mbarrier waits: hgf_mbarrier.cuh
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // a bounded wait gives up after 1 s
 
-// Strip-tiled inverse records (n <= 9) are staged in shared memory by bulk copies
-// (kRecordBuffers blocks per CTA); pixel-major ones (n = 19) are loaded by phase C itself.
+// Inverse records of up to 68 floats (n <= 9) are staged in shared memory by tensor copies
+// (kRecordBuffers boxes per CTA); larger ones (n = 19) are loaded by phase C itself, one coalesced
+// row segment per element.
 template <int B>
-__host__ __device__ constexpr bool stage_records() { return records_strip_tiled(basis_n(B)); }
+__host__ __device__ constexpr bool stage_records() { return records_staged(basis_n(B)); }
 
 
 // CTAs per SM that shared memory leaves room for when the records are staged (r = 9: three at two
@@ -74,21 +75,23 @@ __global__ void __launch_bounds__(NT, (coef_min_blocks<B, K, COMP>())) k_coef(co
                                              const float *__restrict__ img,
                                              const float *__restrict__ shift,
                                              const float *__restrict__ rec,
+                                             const __grid_constant__ CUtensorMap rec_map,
                                              float *__restrict__ coef, int l_first, int n_chunk,
                                              int band_rows, int paper_form, int *status,
                                              const StereoSource stereo) {
   constexpr int NG = basis_n(B), C1 = NG + 1, NC = basis_channels_in(B), RAW = NC + K;
   constexpr int REC = record_floats(NG), CP = coef_floats(NG);
   constexpr bool STAGE = stage_records<B>(), kCoefReload = coef_reload(NG);
-  extern __shared__ __align__(16) float smem[];
-  // layout: 2 mbarriers | two scan buffers | two record rows | (ring)
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+  extern __shared__ __align__(128) float smem_raw[];
+  // layout: record boxes (128-byte aligned, STAGE) | 2 mbarriers | two scan buffers | (ring)
+  const int TW = NT - 2 * r, BW = record_box_width(r);
+  const int RBUF = (REC * BW + 31) / 32 * 32;        // floats per record box, 128-byte multiple
+  float *recs = align_smem128(smem_raw);             // [kRecordBuffers][REC][BW] (STAGE)
+  uint64_t *bars = reinterpret_cast<uint64_t *>(recs + (STAGE ? kRecordBuffers * RBUF : 0));
   // two scan buffers used on alternate rows: a warp may start the next row's vertical update
   // while others still read this row's window sums, so no barrier is needed at the end of a row
-  float *sA0 = smem + 4;
-  const int TW = NT - 2 * r;
-  float *recs = sA0 + 2 * K * C1 * kRowStride;      // [2][REC][TW] record rows (STAGE)
-  float *ring = recs + (STAGE ? kRecordBuffers * REC * TW : 0);  // [2r+1][RAW][NT], private
+  float *sA0 = reinterpret_cast<float *>(bars + 2);
+  float *ring = sA0 + 2 * K * C1 * kRowStride;       // [2r+1][RAW][NT], private
   __shared__ int s_fail;
   const int R = 2 * r + 1;
   const size_t HW = (size_t)H * W;
@@ -110,17 +113,18 @@ __global__ void __launch_bounds__(NT, (coef_min_blocks<B, K, COMP>())) k_coef(co
   float sh[NG];
 #pragma unroll
   for (int i = 0; i < NG; ++i) sh[i] = __ldg(shift + i);
-  // this strip's block of inverse records in row y (REC x TW floats, element-major)
-  const size_t strips = gridDim.y;
-  auto rec_block = [&](int y) { return rec + ((size_t)y * strips + blockIdx.y) * REC * TW; };
-  const uint32_t rec_bytes = (uint32_t)(REC * TW * sizeof(float));
+  // record box of row y: columns [xr, xr + BW), xr = x0 rounded down to a multiple of 4 (the
+  // tensor copy's alignment rule); column x0 + j sits at j + ro
+  const int xr = x0 & ~3, ro = x0 - xr;
+  const size_t rpitch = (size_t)record_pitch(W);
+  const uint32_t rec_bytes = (uint32_t)(REC * BW * sizeof(float));
   // buffer and mbarrier of row y, and the phase parity its copy completes
   auto rbuf = [&](int y) { return kRecordBuffers == 1 ? 0 : (y - Y0) & 1; };
   auto rpar = [&](int y) -> uint32_t {
     return kRecordBuffers == 1 ? (y - Y0) & 1 : ((y - Y0) >> 1) & 1;
   };
   auto issue_records = [&](int y) {  // thread 0 only
-    bulk_copy_g2s(recs + rbuf(y) * REC * TW, rec_block(y), rec_bytes, &bars[rbuf(y)]);
+    tma_load_3d(recs + rbuf(y) * RBUF, &rec_map, xr, y, 0, rec_bytes, &bars[rbuf(y)]);
   };
   if (STAGE) {
     if (t == 0) {
@@ -280,10 +284,12 @@ __global__ void __launch_bounds__(NT, (coef_min_blocks<B, K, COMP>())) k_coef(co
     if (coef_here) {
       const size_t pix = (size_t)y1 * W + x;
       const float invN = 1.f / (float)(clipped_count(x, r, W) * clipped_count(y1, r, H));
-      const float *rrow = recs + rbuf(y1) * REC * TW + t;
-      int stride = TW;  // made opaque per label pair below so that addresses are not hoisted
+      const float *rrow = recs + rbuf(y1) * RBUF + t + ro;
+      const float *grow = rec + (size_t)y1 * rpitch + x;  // plane-major records (not staged)
+      const size_t gplane = (size_t)H * rpitch;
+      int stride = BW;  // made opaque per label pair below so that addresses are not hoisted
       auto recv = [&](int e) -> float {
-        return STAGE ? rrow[e * stride] : __ldg(rec + pix * REC + e);
+        return STAGE ? rrow[e * stride] : __ldg(grow + (size_t)e * gplane);
       };
       if (paper_form) {
         // paper form: v = Mt b~ with b~ = [B(p), B(G~_i p)], the raw window sums (no means)
@@ -553,10 +559,16 @@ __global__ void __launch_bounds__(NT) k_apply(const float *__restrict__ coef, in
 }
 
 
+// Raises a kernel's dynamic shared-memory limit to `bytes`. The default limit (48 KB) covers
+// static and dynamic shared memory together, and the kernels' 128-byte aligned dynamic base may
+// start up to 128 bytes past their static variables, so the limit is raised well before 48 KB.
 template <typename Kern>
 cudaError_t set_smem(Kern k, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (bytes <= 32 * 1024) return cudaSuccess;
+  const cudaError_t e =
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) note_failed("cudaFuncSetAttribute (dynamic shared memory)");
+  return e;
 }
 
 // Rows per band for a kernel whose grid is strips x bands x slabs: the band count that minimises
@@ -582,11 +594,11 @@ static int choose_band_rows(int H, int r, long long strips_slabs, int resident) 
 }
 
 template <typename Kern>
-static int resident_ctas(Kern k, size_t smem) {
+static int resident_ctas(Kern k, size_t smem, int threads = NT) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem) != cudaSuccess) {
     cudaGetLastError();
     per_sm = 1;
   }
@@ -598,7 +610,8 @@ cudaError_t launch_chunk(const hgf_guidance *g, const void *cost, int cost_dtype
                          int nc, float *filtered, float *coef_ws, unsigned long long *keys,
                          unsigned long long *keys2,
                          int band_rows, bool apply_ring, int nominal, int *status,
-                         const StereoSource &stereo, cudaStream_t s, Profiler *prof) {
+                         const StereoSource &stereo, const CUtensorMap &map, cudaStream_t s,
+                         Profiler *prof) {
   const int H = g->H, W = g->W, r = g->r;
   const int TW = NT - 2 * r;
   const unsigned strips = (W + TW - 1) / TW;
@@ -622,10 +635,14 @@ cudaError_t launch_chunk(const hgf_guidance *g, const void *cost, int cost_dtype
                                    : choose_band_rows(H, r, (long long)strips * std::max(1, nominal / 2),
                                                       resident_ctas(k_coef<B, 2, float, false>, sm2));
     dim3 grid(passes, strips, (H + rows - 1) / rows);
+    if (prof) {
+      const int pl[8] = {2, TW, TW, rows, 0, K, nc, (int)(grid.x * grid.y * grid.z)};
+      for (int i = 0; i < 8; ++i) prof->plan[i] = pl[i];
+    }
     LaunchScope ls(prof, "k_coef", s);
 #define HGF_COEF(CT)                                                                          \
   k_coef<B, K, CT, COMP><<<grid, NT, sm, s>>>((const CT *)cost, H, W, r, g->img, g->shift,    \
-                                              g->rec, coef_ws, l_first, nc, rows,             \
+                                              g->rec, map, coef_ws, l_first, nc, rows,        \
                                               g->form == HGF_FORM_PAPER ? 1 : 0, status,      \
                                               stereo);
     switch (cost_dtype) {
@@ -651,6 +668,7 @@ cudaError_t launch_chunk(const hgf_guidance *g, const void *cost, int cost_dtype
                                                           resident_ctas(k_apply<B, true, false>,
                                                                         ring_sm));
         dim3 grid(nc, strips, (H + rows - 1) / rows);
+        if (prof) prof->plan[4] = rows;
         k_apply<B, true, false><<<grid, NT, ring_sm, s>>>(coef_ws, H, W, r, g->img, g->shift,
                                                           keys, keys2, filtered, l_first,
                                                           rows);
@@ -666,6 +684,7 @@ cudaError_t launch_chunk(const hgf_guidance *g, const void *cost, int cost_dtype
                                                         resident_ctas(k_apply<B, false, false>,
                                                                       sm));
       dim3 grid(nc, strips, (H + rows - 1) / rows);
+      if (prof) prof->plan[4] = rows;
       k_apply<B, false, COMP><<<grid, NT, sm, s>>>(coef_ws, H, W, r, g->img, g->shift, keys,
                                                    keys2, filtered, l_first, rows);
     }
@@ -676,28 +695,40 @@ cudaError_t launch_chunk(const hgf_guidance *g, const void *cost, int cost_dtype
 }  // namespace
 
 // Every chunk of labels of one aggregation for basis B (one explicit instantiation per
-// translation unit hgf_fused_*.cu, so that the kernels compile in parallel).
+// translation unit hgf_fused_*.cu, so that the kernels compile in parallel): the single-pass
+// kernel (hgf_onepass.cuh, instantiated for n <= 9) when the plan selects it, else k_coef +
+// k_apply per chunk.
 template <int B>
 cudaError_t launch_basis(const hgf_guidance *g, const void *cost, int cost_dtype, int L,
                          float *filtered, float *coef_ws, unsigned long long *keys,
                          const AggregatePlan &p, int *status, const StereoSource &stereo,
-                         cudaStream_t s, Profiler *prof) {
+                         const CUtensorMap &map, cudaStream_t s, Profiler *prof) {
   cudaError_t e = cudaSuccess;
   unsigned long long *keys2 = keys && p.second ? keys + (size_t)g->H * g->W : nullptr;
+  if constexpr (onepass_built(B)) {
+    if (p.onepass)
+      return launch_onepass<B>(g, cost, cost_dtype, L, filtered, keys, keys2, p, status, stereo,
+                               map, coef_ws, p.onepass_ctas, s, prof);
+  }
+  if (p.onepass) return cudaErrorInvalidValue;
   for (int l0 = 0; l0 < L && e == cudaSuccess; l0 += p.chunk) {
     const int nc = std::min(p.chunk, L - l0);
     if (g->compensated)  // compensated sums: two labels per pass only
       e = launch_chunk<B, 2, true>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys,
-                                   keys2, p.band_rows, false, p.nominal, status, stereo, s, prof);
+                                   keys2, p.band_rows, false, p.nominal, status, stereo, map, s,
+                                   prof);
     else if (p.K == 4)
-      e = launch_chunk<B, 4, false>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys, keys2, p.band_rows,
-                             p.apply_ring, p.nominal, status, stereo, s, prof);
+      e = launch_chunk<B, 4, false>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys, keys2,
+                                    p.band_rows, p.apply_ring, p.nominal, status, stereo, map, s,
+                                    prof);
     else if (p.K == 8)
-      e = launch_chunk<B, 8, false>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys, keys2, p.band_rows,
-                             p.apply_ring, p.nominal, status, stereo, s, prof);
+      e = launch_chunk<B, 8, false>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys, keys2,
+                                    p.band_rows, p.apply_ring, p.nominal, status, stereo, map, s,
+                                    prof);
     else
-      e = launch_chunk<B, 2, false>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys, keys2, p.band_rows,
-                             p.apply_ring, p.nominal, status, stereo, s, prof);
+      e = launch_chunk<B, 2, false>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys, keys2,
+                                    p.band_rows, p.apply_ring, p.nominal, status, stereo, map, s,
+                                    prof);
   }
   return e;
 }
@@ -708,5 +739,5 @@ cudaError_t launch_basis(const hgf_guidance *g, const void *cost, int cost_dtype
   template cudaError_t hgf::launch_basis<B>(const hgf_guidance *, const void *, int, int,      \
                                             float *, float *, unsigned long long *,           \
                                             const hgf::AggregatePlan &, int *,                \
-                                            const hgf::StereoSource &, cudaStream_t,          \
-                                            hgf::Profiler *);
+                                            const hgf::StereoSource &, const CUtensorMap &,   \
+                                            cudaStream_t, hgf::Profiler *);

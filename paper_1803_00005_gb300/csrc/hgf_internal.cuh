@@ -1,6 +1,7 @@
 // Internal declarations of libhgf (CUDA side). Not part of the public ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -38,20 +39,26 @@ inline int packed_size(int n) { return n * (n + 1) / 2; }
 __host__ __device__ constexpr int record_floats(int n) {
   return (n + n * (n + 1) / 2 + 1 + 3) / 4 * 4;
 }
-// Records of up to 68 floats (n <= 9) are stored strip by strip, in the order the fused
-// coefficient kernel stages them in shared memory: strip s of image row y covers columns
-// [s*TW, s*TW + TW) with TW = record_strip_width(r) (the strip width of the fused kernels), and
-// holds record_floats(n) x TW floats element-major (element e of the strip's j-th pixel at
-// e*TW + j). One strip row is one contiguous, 16-byte aligned block; the columns of the last strip
-// past W are padding. Larger records (n = 19) stay pixel-major: H x W x record_floats(n).
-__host__ __device__ constexpr bool records_strip_tiled(int n) { return record_floats(n) <= 68; }
-__host__ __device__ constexpr int record_strip_width(int r) {
-  return kStripThreads - 2 * r > 1 ? kStripThreads - 2 * r : 1;
+// Records are stored plane-major, element e of pixel (x, y) at (e * H + y) * P + x with the row
+// pitch P = record_pitch(W) (W rounded up to 4 floats, so that every row starts 16-byte aligned, as
+// a tensor copy needs). Consecutive threads of a row read and write consecutive addresses. The
+// strip kernels stage the records of one row of their coefficient columns in shared memory with
+// one tensor copy (TMA) of a record_box_width(r) x 1 x REC box whose x origin is rounded down to
+// a multiple of 4 floats (the tensor copy's alignment rule); columns past the image edge arrive
+// as zeros. Records of up to 68 floats (n <= 9) are staged; larger ones (n = 19) are read
+// directly from device memory, one coalesced row segment per element.
+__host__ __device__ constexpr bool records_staged(int n) { return record_floats(n) <= 68; }
+__host__ __device__ constexpr int record_pitch(int W) { return (W + 3) / 4 * 4; }
+// Width of the staged box: the kernels' TW = kStripThreads - 2r coefficient columns plus up to
+// three columns of alignment offset, rounded up to a multiple of 4.
+__host__ __device__ constexpr int record_box_width(int r) {
+  return (kStripThreads - 2 * r + 3 + 3) / 4 * 4;
 }
-inline size_t record_total_floats(int H, int W, int n, int r) {
-  if (!records_strip_tiled(n)) return (size_t)H * W * record_floats(n);
-  const size_t tw = (size_t)record_strip_width(r);
-  return (size_t)H * ((W + tw - 1) / tw) * tw * record_floats(n);
+// The single-pass kernel stages a box of the widest width (r = 0) whatever r is, so that every
+// record element sits at a compile-time offset of the box.
+constexpr int kFusedBoxWidth = record_box_width(0);
+inline size_t record_total_floats(int H, int W, int n) {
+  return (size_t)record_floats(n) * H * record_pitch(W);
 }
 
 #ifndef HGF_RECORD_BUFFERS
@@ -72,7 +79,7 @@ constexpr int kRecordBuffers = HGF_RECORD_BUFFERS;
 // rows ahead like the new rows. Reload where the records are staged (their buffers take the
 // ring's shared memory), the ring otherwise; HGF_COEF_RELOAD = 0 or 1 forces one of them.
 __host__ __device__ constexpr bool coef_reload(int n) {
-  return HGF_COEF_RELOAD < 0 ? records_strip_tiled(n) : HGF_COEF_RELOAD != 0;
+  return HGF_COEF_RELOAD < 0 ? records_staged(n) : HGF_COEF_RELOAD != 0;
 }
 // Per-pixel coefficient record of the fused kernels' workspace: [b, a_1..a_n | padding] rounded
 // up to an even count so that it is read and written as float2 pairs.
@@ -147,6 +154,10 @@ struct NvtxRange {
 struct Profiler {
   bool enabled = false;
   unsigned long long launches = 0;
+  // the last aggregation's plan (hgf_last_plan): path (1 single pass, 2 two kernels, 3 plain),
+  // output columns per strip, coefficient columns per strip, rows per band of the coefficient (or
+  // single-pass) kernel and of the output kernel, labels per pass, labels per chunk, CTAs
+  int plan[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   struct Rec {
     const char *name;
     cudaEvent_t a, b;
@@ -166,7 +177,18 @@ struct Profiler {
   }
 };
 
-// Brackets one kernel launch: counts it and, if profiling is on, records events around it.
+// Name of the first launch or set-up call that failed on this thread since the last error was
+// reported (the API's error message names it), or NULL.
+inline const char *&failed_step() {
+  static thread_local const char *step = nullptr;
+  return step;
+}
+inline void note_failed(const char *what) {
+  if (!failed_step()) failed_step() = what;
+}
+
+// Brackets one kernel launch: counts it and, if profiling is on, records events around it; a
+// launch that fails is noted by name (failed_step).
 class LaunchScope {
  public:
   LaunchScope(Profiler *p, const char *name, cudaStream_t s) : p_(p), name_(name), s_(s) {
@@ -178,6 +200,7 @@ class LaunchScope {
     }
   }
   ~LaunchScope() {
+    if (cudaPeekAtLastError() != cudaSuccess) note_failed(name_);
     if (!p_ || !p_->enabled || !a_) return;
     cudaEvent_t b = p_->get();
     if (!b) return;
@@ -210,7 +233,7 @@ struct hgf_ctx {
   cudaEvent_t io_fork = nullptr, io_done = nullptr;
   hgf_guidance *host_guidance = nullptr;        // reused by hgf_filter_host, hgf_stereo_host
   hgf_guidance *host_guidance_right = nullptr;  // right view of hgf_stereo_host (refinement)
-  hgf_tuning tuning{0, 0, 0, 0};
+  hgf_tuning tuning{0, 0, 0, 0, 0};
   int num_sms = 0;
   hgf::Profiler prof;
 };
@@ -225,7 +248,7 @@ struct hgf_guidance {
   float *G = nullptr;      // n x H x W, shifted guidance G_i - c_i
   float *minv = nullptr;   // n(n+1)/2 x H x W, packed (Sigma + eps E)^-1 (centred form only)
   float *mu = nullptr;     // n x H x W, shifted means A(G_i) - c_i (centred form only)
-  float *rec = nullptr;    // [mu | packed Minv] per pixel (layout: records_strip_tiled)
+  float *rec = nullptr;    // [mu | packed Minv] per pixel, plane-major (record_pitch)
   float *shift = nullptr;  // n, device: c_i (image mean of G_i)
 };
 
@@ -257,6 +280,9 @@ struct AggregatePlan {
   int nominal;      // label count the band heights are planned for: min(64, L rounded up to
                     // even), the same for every chunk of a call so chunking never changes a result
   bool second = false;  // WTA also keeps each pixel's second-smallest key, at keys + H*W
+  bool onepass = false;  // single-pass kernel k_fused (a ring buffer instead of the coefficient
+                         // workspace, one launch)
+  int onepass_ctas = 0;  // its persistent grid
 };
 AggregatePlan plan_aggregate(const hgf_guidance *g, int L, const hgf_tuning &t, int num_sms);
 size_t aggregate_coef_bytes(const hgf_guidance *g, const AggregatePlan &p);
@@ -300,7 +326,28 @@ template <int B>
 cudaError_t launch_basis(const hgf_guidance *g, const void *cost, int cost_dtype, int L,
                          float *filtered, float *coef_ws, unsigned long long *keys,
                          const AggregatePlan &p, int *status, const StereoSource &stereo,
-                         cudaStream_t s, Profiler *prof);
+                         const CUtensorMap &map, cudaStream_t s, Profiler *prof);
+// The single-pass kernel of hgf_onepass.cuh (built for the bases with n <= 9: onepass_built in
+// hgf_basis.cuh).
+template <int B>
+cudaError_t launch_onepass(const hgf_guidance *g, const void *cost, int cost_dtype, int L,
+                           float *filtered, unsigned long long *keys, unsigned long long *keys2,
+                           const AggregatePlan &p, int *status, const StereoSource &stereo,
+                           const CUtensorMap &map, float *ring_ws, int grid_ctas, cudaStream_t s,
+                           Profiler *prof);
+constexpr int kFusedLabels = 2;     // labels per work item of the single-pass kernel
+constexpr int kFusedCtasPerSm = 3;  // resident CTAs per SM its persistent grid is sized for
+// Shared memory of the single-pass kernel, whether the plan may select it for g, and the bytes
+// of its ring buffer for a persistent grid of `ctas` CTAs.
+size_t onepass_smem(int n, int r);
+bool onepass_fits(const hgf_guidance *g);
+size_t onepass_ring_bytes(int n, int r, int ctas);
+// Tensor map of g's plane-major records: a box_w x 1 x record_floats(n) box (box_w = 0:
+// record_box_width(r)).
+cudaError_t make_record_map(const hgf_guidance *g, CUtensorMap *out, int box_w = 0);
+// Commits the allocation-free entry point's static scratch array on `device` (current) and caches
+// its address (hgf_static.cu); hgf_create calls it, and a failure there is not an error.
+cudaError_t static_scratch_init(int device);
 // Reads (and, with clear, resets) the current device's watchdog word set by bounded waits.
 cudaError_t read_device_status(int *status, bool clear);  // fused kernels take this shape
 

@@ -10,6 +10,11 @@ namespace hgf {
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
+// First 128-byte aligned float at or after p in shared memory (a tensor copy's destination).
+__device__ __forceinline__ float *align_smem128(float *p) {
+  const uint32_t a = smem_u32(p);
+  return p + (((128u - (a & 127u)) & 127u) >> 2);
+}
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
@@ -25,6 +30,38 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32
           "r"(smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
+}
+// Thread that issues: expect `bytes` on `bar` and start a tensor copy (TMA) of the box at
+// coordinates (x, y, z) of the tensor map `map` (a __grid_constant__ kernel parameter) into shared
+// `dst` (128-byte aligned). x times the element size must be a multiple of 16 bytes; `bytes` is the
+// whole box, including any part outside the tensor, which arrives as zeros.
+__device__ __forceinline__ void tma_load_3d(void *dst, const void *map, int x, int y, int z,
+                                            uint32_t bytes, uint64_t *bar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+// L2 eviction policy that keeps lines ahead of normally cached data (for buffers that are read
+// back soon and should not be written out to DRAM), and global loads/stores through L2 under it.
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ float ld_l2_hint(const float *a, uint64_t pol) {
+  float v;
+  asm volatile("ld.global.cg.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st_l2_hint(float *a, float v, uint64_t pol) {
+  asm volatile("st.global.cg.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(a), "f"(v), "l"(pol)
+               : "memory");
 }
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;

@@ -113,6 +113,10 @@ cudaError_t launch_aggregate_plain(const hgf_guidance *g, const void *cost, int 
                                    cudaStream_t s, Profiler *prof, float *margin) {
   const int H = g->H, W = g->W, n = g->n, r = g->r;
   const size_t HW = (size_t)H * W;
+  if (prof) {
+    const int pl[8] = {3, W, W, H, H, 1, chunk, 0};
+    for (int i = 0; i < 8; ++i) prof->plan[i] = pl[i];
+  }
   float *A = (float *)ws;
   float *B = A + (size_t)chunk * (n + 1) * HW;
   for (int l0 = 0; l0 < L; l0 += chunk) {

@@ -396,24 +396,16 @@ __global__ void k_moment_cols(const float *__restrict__ rows, int H, int W, int 
 }
 
 // ------------------------------------------------------------------- assembly + HGF inverse
-// Writes one pixel's record in the layout records_strip_tiled(NG) selects.
+// Writes one pixel's record, plane-major with the row pitch record_pitch(W) (consecutive threads
+// write consecutive addresses).
 template <int NG>
-__device__ __forceinline__ void store_record(float *rec, const float *out, int x, int y, int W,
-                                             int r) {
+__device__ __forceinline__ void store_record(float *rec, const float *out, int x, int y, int H,
+                                             int W) {
   constexpr int REC = record_floats(NG);
-  if (records_strip_tiled(NG)) {
-    // strip-tiled, element-major record (consecutive threads write consecutive addresses)
-    const int tw = record_strip_width(r);
-    const int strip = x / tw;
-    float *dst = rec + ((size_t)y * ((W + tw - 1) / tw) + strip) * REC * tw + (x - strip * tw);
+  const size_t P = (size_t)record_pitch(W);
+  float *dst = rec + (size_t)y * P + x;
 #pragma unroll
-    for (int e = 0; e < REC; ++e) dst[(size_t)e * tw] = out[e];
-  } else {
-    float4 *dst = reinterpret_cast<float4 *>(rec + ((size_t)y * W + x) * REC);
-#pragma unroll
-    for (int q = 0; q < REC / 4; ++q)
-      dst[q] = make_float4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
-  }
+  for (int e = 0; e < REC; ++e) dst[(size_t)e * H * P] = out[e];
 }
 
 // Centred form, one thread per pixel, in window-sum units: with the window sums s_i = B(G_i) and
@@ -485,7 +477,7 @@ __global__ void __launch_bounds__(128) k_inverse(const float *__restrict__ mom, 
   for (int e = 0; e < P; ++e) minv[(size_t)e * HW + pix] = out[NG + e];
 #pragma unroll
   for (int i = 0; i < NG; ++i) mu[(size_t)i * HW + pix] = out[i];
-  store_record<NG>(rec, out, x, y, W, r);
+  store_record<NG>(rec, out, x, y, H, W);
 }
 
 // Paper form (Secs. 3-4), one thread per pixel: G_0 = 1 joins the guidance and the uncentred
@@ -562,7 +554,7 @@ __global__ void __launch_bounds__(128) k_inverse_paper(const float *__restrict__
     for (int k = i; k < M; ++k) out[tri_index(M, i, k)] = (float)q(i, k);
 #pragma unroll
   for (int e = PM; e < REC; ++e) out[e] = 0.f;
-  store_record<NG>(rec, out, x, y, W, r);
+  store_record<NG>(rec, out, x, y, H, W);
   (void)P;
 }
 

@@ -78,7 +78,7 @@ struct Slot {
 
 size_t guidance_bytes_for(int C, int H, int W, int n, int r) {
   const size_t HW = (size_t)H * W;
-  return (HW * ((size_t)C + n + packed_size(n) + n) + record_total_floats(H, W, n, r) + 64) *
+  return (HW * ((size_t)C + n + packed_size(n) + n) + record_total_floats(H, W, n) + 64) *
          sizeof(float);
 }
 
@@ -194,7 +194,7 @@ struct hgf_server {
       g.compensated = r.params.compensated;
       const size_t HW = (size_t)r.H * r.W;
       g.rec = (float *)ent->base;
-      g.img = g.rec + record_total_floats(r.H, r.W, g.n, g.r);
+      g.img = g.rec + record_total_floats(r.H, r.W, g.n);
       g.G = g.img + (size_t)g.C * HW;
       g.minv = g.G + (size_t)g.n * HW;
       g.mu = g.minv + (size_t)packed_size(g.n) * HW;
@@ -214,6 +214,10 @@ struct hgf_server {
       AggregatePlan plan = plan_aggregate(&e->g, r.L, t, num_sms);
       const size_t per_label = coef_plane_floats(q->n, (size_t)r.H * r.W) * sizeof(float);
       plan.chunk = std::max(1, std::min(plan.chunk, (int)(sl.ctx->ws_coef.size / per_label)));
+      if (plan.onepass)  // the ring slots that fit the slot's workspace
+        plan.onepass_ctas = std::max(
+            1, std::min(plan.onepass_ctas,
+                        (int)(sl.ctx->ws_coef.size / onepass_ring_bytes(q->n, e->g.r, 1))));
       err = launch_aggregate(&e->g, r.cost, r.cost_dtype, r.L, nullptr, r.labels, r.best,
                              (float *)sl.ctx->ws_coef.ptr,
                              (unsigned long long *)sl.ctx->ws_keys.ptr, plan, sl.stream,
@@ -315,10 +319,12 @@ hgf_status hgf_serve_create(int device, size_t budget_bytes, int slots, int max_
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
   }
   // per-slot workspaces for the largest admitted request: prepare scratch, 16 labels of
-  // coefficient records at n = max_n (fewer labels per chunk are used when a request is bigger),
-  // and the WTA keys
+  // coefficient records at n = max_n (fewer labels per chunk are used when a request is bigger)
+  // or the single-pass kernel's ring buffer at its largest (n = 9, r = 15), and the WTA keys
   const size_t prep = prepare_workspace_bytes(max_n, 1, max_pixels);
-  const size_t coef = (size_t)16 * coef_plane_floats(max_n, (size_t)max_pixels) * sizeof(float);
+  const size_t coef =
+      std::max((size_t)16 * coef_plane_floats(max_n, (size_t)max_pixels) * sizeof(float),
+               onepass_ring_bytes(9, 15, s->num_sms * kFusedCtasPerSm));
   const size_t keys = (size_t)max_pixels * sizeof(unsigned long long);
   s->slot_bytes = (size_t)slots * (prep + coef + keys);
   if (s->slot_bytes > budget_bytes) return cleanup(HGF_ENOMEM);

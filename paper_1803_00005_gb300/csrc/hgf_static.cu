@@ -3,13 +3,17 @@
 // cudaFree can synchronise the device and block for an unbounded time), or a plugin inside a host
 // program that hands out all device memory from its own allocator at start-up, so that a late
 // cudaMalloc fails or fragments the host's pool. Instead of
-// the context's growable workspace, this entry point takes its scratch (the per-pixel WTA keys and
-// the per-chunk coefficient planes) from one file-scope device array of fixed size, which every
-// GPU that loads this library holds until the process exits.
+// the context's growable workspace, this entry point takes its scratch (the per-pixel WTA keys and,
+// on the two-kernel path, the per-chunk coefficient planes) from one file-scope device array of
+// fixed size, which every GPU that loads this library holds until the process exits.
 //
-// Set-up: the first call on a device (with that device current) looks up the array's device
-// address with cudaGetSymbolAddress; make that first call before any stream capture. After that a
-// call allocates nothing and only enqueues a memset and kernels on `stream`.
+// Set-up: hgf_create looks up the array's device address with cudaGetSymbolAddress, with the
+// context's device current. That lookup loads this file's device module, which is when the array
+// is committed on that device (under lazy module loading it would otherwise be committed by the
+// first call of this entry point). If it failed there (no memory left), the entry point tries
+// again on its first call and returns HGF_ENOMEM, without marking the context failed, while it
+// keeps failing; make the first call before any stream capture in that case. Once the address is
+// known a call allocates nothing and only enqueues a memset and kernels on `stream`.
 //
 // Every call shares the one array, and it keeps the previous call's contents: the WTA keys are
 // reset at the start of each call and every coefficient plane is written before it is read.
@@ -31,6 +35,7 @@ void *g_static_ptr[kMaxDevices] = {};
 
 // Device address of the array on `device` (current), looked up once per device.
 cudaError_t static_scratch(int device, void **out) {
+  if (!out) return cudaErrorInvalidValue;
   if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(g_static_mu);
   if (!g_static_ptr[device]) {
@@ -44,6 +49,14 @@ cudaError_t static_scratch(int device, void **out) {
 }
 
 }  // namespace
+
+namespace hgf {
+// Commits the array on `device` (current) and caches its address; called by hgf_create.
+cudaError_t static_scratch_init(int device) {
+  void *p = nullptr;
+  return static_scratch(device, &p);
+}
+}  // namespace hgf
 
 extern "C" hgf_status hgf_aggregate_static(hgf_ctx *ctx, const hgf_guidance *g, const void *cost,
                                            int cost_dtype, int L, void *filtered,
@@ -75,23 +88,35 @@ extern "C" hgf_status hgf_aggregate_static(hgf_ctx *ctx, const hgf_guidance *g, 
   hgf::AggregatePlan plan = hgf::plan_aggregate(g, L, ctx->tuning, ctx->num_sms);
   const size_t HW = (size_t)g->H * g->W;
   const size_t keys_bytes = (HW * sizeof(unsigned long long) + 255) / 256 * 256;
-  const size_t per_label = hgf::coef_plane_floats(g->n, HW) * sizeof(float);
-  if (keys_bytes + per_label > kStaticScratchBytes)
+  // the single-pass kernel needs the keys and one ring slot per CTA of its persistent grid (the
+  // grid shrinks to what fits); the two-kernel path one coefficient plane per label of a chunk
+  const size_t per_unit = plan.onepass
+                              ? hgf::onepass_ring_bytes(g->n, g->r, 1)
+                              : hgf::coef_plane_floats(g->n, HW) * sizeof(float);
+  if (keys_bytes + per_unit > kStaticScratchBytes)
     return fail(HGF_EUNSUPPORTED,
                 "image too large for the " + std::to_string(kStaticScratchBytes >> 20) +
-                    " MiB static scratch: needs " + std::to_string(keys_bytes + per_label) +
-                    " bytes for one label; use hgf_aggregate");
-  const int fit = (int)((kStaticScratchBytes - keys_bytes) / per_label);
-  plan.chunk = std::max(1, std::min(plan.chunk, fit));
+                    " MiB static scratch: needs " + std::to_string(keys_bytes + per_unit) +
+                    " bytes; use hgf_aggregate");
+  const int fit = (int)((kStaticScratchBytes - keys_bytes) / per_unit);
+  if (plan.onepass)
+    plan.onepass_ctas = std::max(1, std::min(plan.onepass_ctas, fit));
+  else
+    plan.chunk = std::max(1, std::min(plan.chunk, fit));
 
   void *base = nullptr;
   e = static_scratch(ctx->device, &base);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // not sticky: the context stays usable
+    return fail(HGF_ENOMEM, std::string("the static scratch array is not available on this "
+                                        "device: ") + cudaGetErrorString(e));
+  }
   hgf::Profiler count_only;  // counts launches, records no events
   e = hgf::launch_aggregate(g, cost, cost_dtype, L, (float *)filtered, labels, best,
                             (float *)((char *)base + keys_bytes), (unsigned long long *)base,
                             plan, (cudaStream_t)stream, &count_only);
   ctx->prof.launches += count_only.launches;
+  for (int i = 0; i < 8; ++i) ctx->prof.plan[i] = count_only.plan[i];
   if (e != cudaSuccess) return cuda_fail(e, "launch");
   return HGF_OK;
 }

@@ -33,7 +33,8 @@ EXPORTED = [
     "hgf_create", "hgf_destroy", "hgf_last_error", "hgf_num_channels", "hgf_make_guidance",
     "hgf_prepare", "hgf_guidance_release", "hgf_guidance_info", "hgf_guidance_export",
     "hgf_aggregate", "hgf_aggregate_plain", "hgf_wta", "hgf_filter_host", "hgf_set_tuning",
-    "hgf_guidance_update", "hgf_launch_count", "hgf_profile_enable", "hgf_profile_report",
+    "hgf_guidance_update", "hgf_launch_count", "hgf_last_plan", "hgf_profile_enable",
+    "hgf_profile_report",
     "hgf_aggregate_static", "hgf_serve_create", "hgf_serve_submit", "hgf_serve_poll",
     "hgf_serve_wait", "hgf_serve_stats", "hgf_serve_inject_alloc_failures", "hgf_serve_destroy",
     "hgf_batch_create", "hgf_batch_run", "hgf_batch_launch_graph", "hgf_batch_destroy",
@@ -64,7 +65,8 @@ class hgf_cost_params(ctypes.Structure):
 
 class hgf_tuning(ctypes.Structure):
     _fields_ = [("labels_per_pass", ctypes.c_int), ("band_rows", ctypes.c_int),
-                ("chunk_labels", ctypes.c_int), ("apply_mode", ctypes.c_int)]
+                ("chunk_labels", ctypes.c_int), ("apply_mode", ctypes.c_int),
+                ("kernel", ctypes.c_int)]
 
 
 class hgf_request(ctypes.Structure):
@@ -141,6 +143,7 @@ def lib():
         "hgf_set_tuning": (c_int, [vp, P(hgf_tuning)]),
         "hgf_guidance_update": (c_int, [vp, vp, vp, vp]),
         "hgf_launch_count": (c_int, [vp, P(ctypes.c_ulonglong)]),
+        "hgf_last_plan": (c_int, [vp, P(c_int), c_int]),
         "hgf_device_status": (c_int, [vp, P(c_int), c_int]),
         "hgf_watchdog_probe": (c_int, [vp, c_int, vp]),
         "hgf_stereo_host": (c_int, [vp, vp, vp, c_int, c_int, c_int, c_int, P(hgf_params),
@@ -339,9 +342,10 @@ def hgf_filter_host(ctx, img, cost, cost_dtype, params, labels, best=None, strea
     _check(ctx, st)
 
 
-def hgf_set_tuning(ctx, labels_per_pass=0, band_rows=0, chunk_labels=0, apply_mode=0):
+def hgf_set_tuning(ctx, labels_per_pass=0, band_rows=0, chunk_labels=0, apply_mode=0, kernel=0):
+    """kernel: 0 automatic, 1 single pass (n <= 9), 2 coefficient + output kernels."""
     t = hgf_tuning(labels_per_pass=labels_per_pass, band_rows=band_rows,
-                   chunk_labels=chunk_labels, apply_mode=apply_mode)
+                   chunk_labels=chunk_labels, apply_mode=apply_mode, kernel=kernel)
     _check(ctx, lib().hgf_set_tuning(ctx, ctypes.byref(t)))
 
 
@@ -354,6 +358,18 @@ def hgf_launch_count(ctx):
     v = ctypes.c_ulonglong()
     _check(ctx, lib().hgf_launch_count(ctx, ctypes.byref(v)))
     return v.value
+
+
+PLAN_FIELDS = ("path", "out_strip", "coef_strip", "band_rows", "apply_band_rows",
+               "labels_per_pass", "chunk", "ctas")
+
+
+def hgf_last_plan(ctx):
+    """The plan of ctx's last aggregation as a dict (PLAN_FIELDS; path 1 single pass, 2 two
+    kernels, 3 plain)."""
+    arr = (ctypes.c_int * 8)()
+    _check(ctx, lib().hgf_last_plan(ctx, arr, 8))
+    return dict(zip(PLAN_FIELDS, list(arr)))
 
 
 def hgf_batched_inverse(ctx, S, n, lam, method="prop1", precision="f64", out=None, stream=None):
@@ -439,7 +455,7 @@ def hgf_autotune(ctx, g, cost, labels, reps=3, stream=None):
                                    _ptr(labels), int(reps), ctypes.byref(t), ctypes.byref(n),
                                    _stream(stream)))
     return dict(labels_per_pass=t.labels_per_pass, band_rows=t.band_rows,
-                chunk_labels=t.chunk_labels, apply_mode=t.apply_mode), n.value
+                chunk_labels=t.chunk_labels, apply_mode=t.apply_mode, kernel=t.kernel), n.value
 
 
 def autotune_cached(ctx, g, cost, labels, cache_path, reps=3, stream=None):

@@ -28,7 +28,8 @@ def cost_tensor(torch, cost, dtype):
 
 def run_path(ctx, guidance, cost, dtype, degree, r, eps, basis="monomial", plain=False,
              inv_precision="f64", combine="alpha", want_filtered=True, form="centred",
-             compensated=False):
+             compensated=False, kernel=0):
+    """kernel: hgf_tuning.kernel for the call (0 automatic, 1 single pass, 2 two kernels)."""
     torch = torch_cuda()
     from paper_1803_00005_gb300 import hgf
     img = torch.from_numpy(np.ascontiguousarray(guidance, dtype=np.float32)).cuda()
@@ -43,8 +44,14 @@ def run_path(ctx, guidance, cost, dtype, degree, r, eps, basis="monomial", plain
         labels = torch.empty((H, W), dtype=torch.int32, device="cuda")
         best = torch.empty((H, W), dtype=torch.float32, device="cuda")
         fn = hgf.hgf_aggregate_plain if plain else hgf.hgf_aggregate
-        fn(ctx, g, c, filtered=filt, labels=labels, best=best)
-        torch.cuda.synchronize()
+        if kernel:
+            hgf.hgf_set_tuning(ctx, kernel=kernel)
+        try:
+            fn(ctx, g, c, filtered=filt, labels=labels, best=best)
+            torch.cuda.synchronize()
+        finally:
+            if kernel:
+                hgf.hgf_set_tuning(ctx)
     finally:
         hgf.hgf_guidance_release(g)
     return (None if filt is None else filt.cpu().numpy()), labels.cpu().numpy(), best.cpu().numpy()
@@ -87,3 +94,23 @@ def oracle_case(width, height, L, seed, degree, r, eps, dtype="f32", basis="mono
     case = synth.make_case(width, height, L, seed, dtype)
     ref = O.centred_filter(case.guidance, synth.from_dtype(case.cost, dtype), r, eps, degree, basis)
     return case, ref
+
+
+def boundary_regions(plan, H, W, half=3, extra=(), limit=None):
+    """Rectangles of (2 half)^2 pixels centred on crossings of the band boundary rows of the plan's
+    kernels (hgf_last_plan) with its strip boundary columns (at most `limit` crossings, spread
+    over the image), plus the four corners, the centre and `extra` centres."""
+    rows = sorted({k * b for b in (plan["band_rows"], plan["apply_band_rows"]) if b > 0
+                   for k in range(1, (H + b - 1) // b) if 0 < k * b < H})
+    cols = sorted({k * plan["out_strip"] for k in range(1, W) if 0 < k * plan["out_strip"] < W}
+                  if plan["out_strip"] > 0 else [])
+    cross = [(y, x) for y in rows for x in cols]
+    if limit is not None and len(cross) > limit:
+        cross = [cross[i * len(cross) // limit] for i in range(limit)]
+    centres = cross + [(half, half), (half, W - half), (H - half, half), (H - half, W - half),
+                       (H // 2, W // 2)] + list(extra)
+    regions = []
+    for y, x in centres:
+        y0, x0 = min(max(0, y - half), H - 2 * half), min(max(0, x - half), W - 2 * half)
+        regions.append((y0, y0 + 2 * half, x0, x0 + 2 * half))
+    return sorted(set(regions))

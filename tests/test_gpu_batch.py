@@ -1,5 +1,6 @@
 """Batches (hgf_batch_*): many mixed-size jobs forked over internal streams, run directly and as
-one captured CUDA graph, give the same results as each job prepared and aggregated alone."""
+one captured CUDA graph, give the same results as each job prepared and aggregated alone; the
+degree-3 and bfloat16 jobs also match the float64 oracle directly."""
 import numpy as np
 import pytest
 
@@ -40,7 +41,7 @@ def test_batch_equals_alone_direct_and_graph():
             out_l = torch.full_like(lab, -1)
             out_b = torch.full_like(best, float("nan"))
             items.append(dict(img=img, cost=cost, p=p, ref=(lab.cpu().numpy(), best.cpu().numpy()),
-                              out=(out_l, out_b)))
+                              out=(out_l, out_b), case=case, spec=sp))
         jobs = [hgf.make_job(it["img"], it["cost"], it["p"], labels=it["out"][0],
                              best=it["out"][1]) for it in items]
         batch = hgf.hgf_batch_create(ctx, jobs, streams=3)
@@ -55,6 +56,18 @@ def test_batch_equals_alone_direct_and_graph():
                 for it in items:
                     assert np.array_equal(it["out"][0].cpu().numpy(), it["ref"][0])
                     assert np.array_equal(it["out"][1].cpu().numpy(), it["ref"][1])
+            # batched results against the oracle directly: the degree-3 (n = 19) job and the
+            # bfloat16 one
+            from oracle import hgf_oracle as O
+            from gpu_helpers import check_against_oracle
+            for it in items:
+                sp = it["spec"]
+                if sp["degree"] == 3 or sp.get("dtype") == "bf16":
+                    ref = O.centred_filter(it["case"].guidance,
+                                           synth.from_dtype(it["case"].cost, sp.get("dtype", "f32")),
+                                           sp["r"], 1e-4, sp["degree"])
+                    check_against_oracle(None, it["out"][0].cpu().numpy(),
+                                         it["out"][1].cpu().numpy(), ref)
         finally:
             hgf.hgf_batch_destroy(batch)
     finally:

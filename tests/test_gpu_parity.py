@@ -9,8 +9,8 @@ import pytest
 from oracle import hgf_oracle as O
 from paper_1803_00005_gb300 import synth
 
-from gpu_helpers import (check_against_oracle, normwise, oracle_case, run_path, torch_cuda,
-                         cost_tensor)
+from gpu_helpers import (boundary_regions, check_against_oracle, normwise, oracle_case, run_path,
+                         torch_cuda, cost_tensor)
 
 pytestmark = pytest.mark.gpu
 
@@ -25,20 +25,24 @@ def ctx():
     hgf.hgf_destroy(c)
 
 
-@pytest.mark.parametrize("plain", [False, True])
-def test_small_stereo_n3(ctx, plain):
+PATHS = {"single-pass": dict(kernel=1), "two-kernel": dict(kernel=2), "plain": dict(plain=True)}
+
+
+@pytest.mark.parametrize("path", list(PATHS))
+def test_small_stereo_n3(ctx, path):
     """64x48, L=16, degree 1 (n=3), r=4, eps=1e-4 (the small stereo configuration), in full."""
     case, ref = oracle_case(64, 48, 16, 1, degree=1, r=4, eps=1e-4)
-    q, labels, best = run_path(ctx, case.guidance, case.cost, "f32", 1, 4, 1e-4, plain=plain)
+    q, labels, best = run_path(ctx, case.guidance, case.cost, "f32", 1, 4, 1e-4, **PATHS[path])
     check_against_oracle(q, labels, best, ref)
 
 
-@pytest.mark.parametrize("plain", [False, True])
-def test_n9_several_strips_ragged(ctx, plain):
-    """n=9, r=9 on 300x170 with 11 labels: 3 strips (last ragged), several bands, label passes
-    4+4+3."""
+@pytest.mark.parametrize("path", list(PATHS))
+def test_n9_several_strips_ragged(ctx, path):
+    """n=9, r=9 on 300x170 with 11 labels: several strips (the last ragged: 4 strips of 92
+    output columns for the single-pass kernel, 3 of 110 for the two-kernel path), several bands,
+    label passes 2+2+..+1 on the two-kernel path."""
     case, ref = oracle_case(300, 170, 11, 21, degree=2, r=9, eps=1e-4)
-    q, labels, best = run_path(ctx, case.guidance, case.cost, "f32", 2, 9, 1e-4, plain=plain)
+    q, labels, best = run_path(ctx, case.guidance, case.cost, "f32", 2, 9, 1e-4, **PATHS[path])
     check_against_oracle(q, labels, best, ref)
 
 
@@ -104,8 +108,8 @@ def test_edge_shapes(ctx, W, H, L, r, degree):
     guid = g.uniform(size=(3, H, W)).astype(np.float32)
     cost = (g.uniform(size=(L, H, W)) * 0.03).astype(np.float32)
     ref = O.centred_filter(guid, cost.astype(np.float64), r, 1e-3, degree)
-    for plain in (False, True):
-        q, labels, best = run_path(ctx, guid, cost, "f32", degree, r, 1e-3, plain=plain)
+    for path in PATHS.values():
+        q, labels, best = run_path(ctx, guid, cost, "f32", degree, r, 1e-3, **path)
         check_against_oracle(q, labels, best, ref)
 
 
@@ -184,27 +188,41 @@ def test_filter_host_end_to_end(ctx):
     assert np.array_equal(labels, l2) and np.array_equal(best, b2)
 
 
-def test_quarter_size_n9_sampled(ctx):
-    """The 450x375 / 60-label / n=9 / r=9 workload in full on the GPU, in the launch
-    configuration the benchmark times; checked on sampled pixels (borders, corners, interior)
-    where the oracle runs on the exact crop each output depends on."""
+@pytest.mark.parametrize("path", ["two-kernel", "single-pass"])
+def test_quarter_size_n9_regions(ctx, path):
+    """The 450x375 / 60-label / n=9 / r=9 workload in full on the GPU, in the launch configuration
+    the benchmark times (the automatic plan of each path), checked against the oracle on every
+    pixel of rectangles around each crossing of a band boundary with a strip boundary that the
+    plan produced, the corners and random interior points (the oracle runs on the exact crop each
+    rectangle depends on); labels exact where the oracle's margin exceeds 1e-3. At full size: all
+    values finite, labels index the minimum of the returned volume."""
+    from paper_1803_00005_gb300 import hgf
     c = synth.CONFIG_QUARTER
     case = synth.make_case(c["width"], c["height"], c["n_labels"], c["seed"], "f32")
-    q, labels, best = run_path(ctx, case.guidance, case.cost, "f32", c["degree"], c["r"], c["eps"])
+    q, labels, best = run_path(ctx, case.guidance, case.cost, "f32", c["degree"], c["r"], c["eps"],
+                               kernel=1 if path == "single-pass" else 0)
+    plan = hgf.hgf_last_plan(ctx)
+    assert plan["path"] == (1 if path == "single-pass" else 2)
     H, W = c["height"], c["width"]
     g = np.random.Generator(np.random.PCG64(123))
-    pts = [(0, 0), (0, W - 1), (H - 1, 0), (H - 1, W - 1), (9, 9), (H // 2, W // 2), (18, W - 19),
-           (H - 10, 110), (200, 111), (101, 329)]
-    pts += [(int(y), int(x)) for y, x in zip(g.integers(0, H, 14), g.integers(0, W, 14))]
-    ref = O.filter_at(case.guidance, case.cost, c["r"], c["eps"], c["degree"], pts)
-    got = np.stack([q[:, y, x] for y, x in pts], axis=1)
+    extra = [(int(y), int(x)) for y, x in zip(g.integers(10, H - 10, 6), g.integers(10, W - 10, 6))]
+    regions = boundary_regions(plan, H, W, extra=extra)
+    assert len(regions) > 8, plan
     scale = max(float(np.max(np.abs(q))), 1e-30)
-    assert np.max(np.abs(got - ref)) / scale <= 1e-4
-    ol, _, om = O.wta(ref[:, :, None])
-    gl = np.array([labels[y, x] for y, x in pts])
-    sure = om[:, 0] > 1e-3
-    assert np.array_equal(gl[sure], ol[sure, 0])
-    # properties at full size: labels index the minimum of the returned volume, all finite
+    npx = 0
+    for y0, y1, x0, x1 in regions:
+        ref = O.filter_region(case.guidance, case.cost, c["r"], c["eps"], c["degree"],
+                              y0, y1, x0, x1)
+        got = q[:, y0:y1, x0:x1]
+        assert np.max(np.abs(got - ref)) / scale <= 1e-4, (y0, x0)
+        ol, ob, om = O.wta(ref)
+        gl = labels[y0:y1, x0:x1]
+        sure = om > 1e-3
+        assert np.array_equal(gl[sure], ol[sure]), (y0, x0)
+        picked = np.take_along_axis(ref, gl[None].astype(np.int64), axis=0)[0]
+        assert np.all(picked - ob <= 1e-4 * scale)
+        npx += (y1 - y0) * (x1 - x0)
+    assert npx >= 256, npx
     assert np.all(np.isfinite(q))
     picked = np.take_along_axis(q, labels[None].astype(np.int64), axis=0)[0]
     assert np.array_equal(picked, q.min(axis=0))
@@ -229,15 +247,16 @@ def test_invalid_arguments_rejected(ctx):
 
 
 def test_results_independent_of_label_chunking(ctx):
-    """Label chunking (workspace size) and labels per pass do not change any result bit: the band
-    boundaries of the running sums depend on the image shape only. (Explicit band_rows or
-    apply_mode tuning does change the rounding, within the tolerance.)"""
+    """On the two-kernel path, label chunking (workspace size) and labels per pass do not change
+    any result bit: the band boundaries of the running sums depend on the image shape only.
+    (Explicit band_rows or apply_mode tuning does change the rounding, within the tolerance.)"""
     from paper_1803_00005_gb300 import hgf
     case = synth.make_case(330, 210, 23, 111)
+    hgf.hgf_set_tuning(ctx, kernel=2)
     base = run_path(ctx, case.guidance, case.cost, "f32", 2, 9, 1e-4)
     try:
         for chunk, K in ((5, 2), (1, 2), (8, 4), (23, 4)):
-            hgf.hgf_set_tuning(ctx, labels_per_pass=K, chunk_labels=chunk)
+            hgf.hgf_set_tuning(ctx, labels_per_pass=K, chunk_labels=chunk, kernel=2)
             got = run_path(ctx, case.guidance, case.cost, "f32", 2, 9, 1e-4)
             assert np.array_equal(got[0], base[0]) and np.array_equal(got[1], base[1])
     finally:

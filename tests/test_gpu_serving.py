@@ -1,5 +1,6 @@
 """Serving loop (hgf_serve_*): results of requests run in a mix of concurrent requests equal the
-results of the same requests run alone; guidance reuse, admission by memory budget, queue limits,
+results of the same requests run alone, and the degree-3 and bfloat16 requests match the float64
+oracle directly; guidance reuse, admission by memory budget, queue limits,
 bounded waits and injected allocation failures behave as documented. Failures are made on the
 host (an allocation made to fail, a budget too small, a wait with a short limit): no GPU fault."""
 import numpy as np
@@ -20,8 +21,19 @@ def make_inputs(torch, specs):
             cost = torch.from_numpy(case.cost.view(np.int16)).cuda().view(torch.bfloat16)
         else:
             cost = torch.from_numpy(case.cost).cuda()
-        out.append(dict(sp, img=img, cost=cost))
+        out.append(dict(sp, img=img, cost=cost, case=case))
     return out
+
+
+def oracle_check(item, labels, best):
+    """A served (or batched) result against the float64 oracle on the same (rounded) inputs."""
+    from oracle import hgf_oracle as O
+    from paper_1803_00005_gb300 import synth
+    from gpu_helpers import check_against_oracle
+    case = item["case"]
+    ref = O.centred_filter(case.guidance, synth.from_dtype(case.cost, item.get("dtype", "f32")),
+                           item["r"], 1e-4, item["degree"])
+    check_against_oracle(None, labels, best, ref)
 
 
 def alone(torch, hgf, ctx, item):
@@ -75,6 +87,10 @@ def test_mix_equals_alone_and_cache_reuse():
         for (lab, best), (rl, rb) in zip(outs, refs):
             assert np.array_equal(lab.cpu().numpy(), rl)
             assert np.array_equal(best.cpu().numpy(), rb)
+        # served results against the oracle directly: the degree-3 (n = 19) request and the
+        # bfloat16 one
+        for k in (3, 4):
+            oracle_check(items[k], outs[k][0].cpu().numpy(), outs[k][1].cpu().numpy())
         stats = hgf.hgf_serve_stats(srv)
         assert stats["completed"] == len(items)
         assert stats["cache_hits"] >= 1

@@ -1,8 +1,9 @@
 """CPU checks of the device-memory layouts the fused kernels index, on the library's own code.
 
 The coefficient workspace (one plane per label, tiled by 32 pixels: coef_pair_index,
-coef_plane_floats) and the strip-tiled inverse records (record_total_floats, record_strip_width)
-are computed by host-and-device inline functions of the CUDA sources. This test compiles those
+coef_plane_floats), the plane-major inverse records (record_pitch, record_total_floats) and the
+boxes the strip kernels stage from them by tensor copies (record_box_width) are computed by
+host-and-device inline functions of the CUDA sources. This test compiles those
 functions into a small host program with nvcc (no GPU is used) and checks, over many image sizes,
 basis sizes and radii, that every index the kernels form is inside the buffer the host sizes for
 it and that no two records share a slot: a layout mistake here would be an out-of-bounds write on
@@ -57,27 +58,54 @@ int main() {
         }
     }
   }
-  // strip-tiled inverse records: block (y, s) of REC x TW floats, element e of pixel j at e*TW + j
-  for (int n : {1, 3, 9}) {
+  // plane-major inverse records: element e of (x, y) at (e * H + y) * P + x, P = record_pitch(W)
+  for (int n : {1, 3, 9, 19}) {
     const int REC = record_floats(n);
-    if (!records_strip_tiled(n) || REC % 4) return fail("record_floats", n, 0, 0);
-    for (int r : {0, 1, 4, 9, 20, 63}) {
-      const size_t TW = record_strip_width(r);
-      for (auto &hw : shapes) {
-        const size_t H = hw[0], W = hw[1];
-        const size_t total = record_total_floats(H, W, n, r);
-        const size_t strips = (W + TW - 1) / TW;
-        std::vector<unsigned char> used(total, 0);
-        for (size_t y = 0; y < H; ++y)
-          for (size_t x = 0; x < W; ++x)
-            for (int e = 0; e < REC; ++e) {
-              const size_t s = x / TW, j = x % TW;
-              const size_t i = (y * strips + s) * REC * TW + (size_t)e * TW + j;
-              if (i >= total) return fail("record index out of range", n, H, W);
-              if (used[i]++) return fail("record index collision", n, H, W);
-            }
-        // each block starts 16-byte aligned (the bulk copy's requirement)
-        if ((REC * TW * sizeof(float)) % 16) return fail("record block alignment", n, H, W);
+    if (REC % 4) return fail("record_floats", n, 0, 0);
+    for (auto &hw : shapes) {
+      const size_t H = hw[0], W = hw[1], P = record_pitch((int)W);
+      if (P < W || P % 4 || P >= W + 4) return fail("record pitch", n, H, W);
+      const size_t total = record_total_floats((int)H, (int)W, n);
+      std::vector<unsigned char> used(total, 0);
+      for (int e = 0; e < REC; ++e)
+        for (size_t y = 0; y < H; ++y) {
+          // every row of every element plane starts 16-byte aligned (the tensor map's strides)
+          if ((((size_t)e * H + y) * P * sizeof(float)) % 16) return fail("row alignment", n, H, W);
+          for (size_t x = 0; x < W; ++x) {
+            const size_t i = ((size_t)e * H + y) * P + x;
+            if (i >= total) return fail("record index out of range", n, H, W);
+            if (used[i]++) return fail("record index collision", n, H, W);
+          }
+        }
+    }
+  }
+  // staged record boxes: both strip kernels load columns [xr, xr + BW) of one row with xr a
+  // multiple of 4; every coefficient column a thread reads lies in the box, at a box index < BW
+  for (int r : {0, 1, 4, 9, 20, 24, 40, 63}) {
+    const int BW = record_box_width(r), TW = kStripThreads - 2 * r;
+    if (BW % 4 || BW > 256 || BW < TW + 3) return fail("box width", r, 0, 0);
+    for (auto &hw : shapes) {
+      const long W = (long)hw[1];
+      // k_coef: strip s, coefficient columns x0 + t for t < TW, box index t + ro
+      for (long x0 = 0; x0 < W; x0 += TW) {
+        const long xr = x0 & ~3L, ro = x0 - xr;
+        if (xr % 4 || ro < 0 || ro > 3) return fail("k_coef box origin", r, 0, (size_t)W);
+        for (long t = 0; t < TW; ++t)
+          if (t + ro >= BW || x0 + t < xr || x0 + t >= xr + BW) return fail("k_coef box", r, 0, W);
+      }
+      // k_fused: output strip of 128 - 4r columns at x0; coefficient columns x0 - 2r + t for
+      // t in [r, 128 - r), box index t - r + ro, in a box kFusedBoxWidth wide
+      const int TWo = kStripThreads - 4 * r;
+      if (kFusedBoxWidth < BW || kFusedBoxWidth % 4 || kFusedBoxWidth > 256)
+        return fail("k_fused box width", r, 0, W);
+      if (TWo < 32) continue;
+      for (long x0 = 0; x0 < W; x0 += TWo) {
+        const long c0 = x0 - r, xr = c0 & ~3L, ro = c0 - xr;
+        if (((xr % 4) + 4) % 4 || ro < 0 || ro > 3) return fail("k_fused box origin", r, 0, W);
+        for (long t = r; t < kStripThreads - r; ++t) {
+          const long x = x0 - 2 * r + t, j = t - r + ro;
+          if (j < 0 || j >= kFusedBoxWidth || x != xr + j) return fail("k_fused box", r, 0, W);
+        }
       }
     }
   }
