@@ -36,8 +36,13 @@ WORKLOADS = {
     "large": dict(width=1400, height=1100, n_labels=256, degree=2, r=9, eps=1e-4, dtype="bf16",
                   seed=3, name="stereo 1400x1100, L=256, n=9, r=9, eps=1e-4, bf16 costs"),
 }
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+FP32_LANES_PER_SM = 128                              # FP32 FMA lanes per SM (Blackwell)
 FP64_PEAK_TFLOPS = 1.25                              # nominal GB300 FP64 rate
+
+
+def fp32_peak_tflops(sm_count: int, sm_mhz: float) -> float:
+    """FP32 FMA peak from the queried SM count and an SM clock: SMs x 128 lanes x 2 flops."""
+    return sm_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
 
 def flops_per_unit(kernel: str, n: int) -> tuple[float, str] | None:
@@ -102,6 +107,10 @@ def parse():
     ap.add_argument("--inv-precision", choices=["f64", "df64", "f32"], default="f64",
                     help="arithmetic of the covariance assembly + inverse")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the warm, plain-form, single-pass and served legs of the line")
+    ap.add_argument("--serve-rate", type=float, default=20.0,
+                    help="requests per second of the default line's short served leg")
     ap.add_argument("--cpu-crop", type=int, nargs=2, default=(225, 188),
                     help="width height of the centred crop the CPU baseline runs on")
     ap.add_argument("--serve", action="store_true",
@@ -307,19 +316,18 @@ def batch_arm(args):
     print(json.dumps(line), flush=True)
 
 
-def serve_arm(args):
+def run_serving(rate, duration, warm, slots, device=0):
     """Open-loop serving: requests arrive at Poisson times (synth.serving_requests: sizes
     640x480 .. 1920x1080, L 64..256, degree 1..3, r in {4, 9}, bf16 costs, 30% reuse an earlier
     guidance) and are submitted to hgf_serve at their arrival time; latency counts from the
     scheduled arrival. Inputs come from a pool of device-resident stereo pairs per size (costs
-    built on the device before the clock starts)."""
+    built on the device before the clock starts). Returns hgf_serve_stats after the run (the
+    statistics are reset once the warm-up's arrivals are submitted)."""
     import numpy as np
     import torch
-    from paper_1803_00005_gb300 import build, hgf, synth
-    build.build()
-    torch.cuda.set_device(0)
-    n_req = int(args.rate * (args.duration + args.warm)) + 1
-    reqs = synth.serving_requests(n_req, rate_hz=args.rate, seed=5)
+    from paper_1803_00005_gb300 import hgf, synth
+    n_req = int(rate * (duration + warm)) + 1
+    reqs = synth.serving_requests(n_req, rate_hz=rate, seed=5)
     pool = {}
     for sp in reqs:
         key = (sp["width"], sp["height"])
@@ -330,7 +338,7 @@ def serve_arm(args):
                              labels=torch.empty((sp["height"], sp["width"]), dtype=torch.int32,
                                                 device="cuda"))
     torch.cuda.synchronize()
-    srv = hgf.hgf_serve_create(0, budget_bytes=120 << 30, slots=args.slots, max_queue=4096,
+    srv = hgf.hgf_serve_create(device, budget_bytes=120 << 30, slots=slots, max_queue=4096,
                                max_pixels=1920 * 1080, max_n=19)
     t0 = time.perf_counter() + 0.5
     ids, measured = [], []
@@ -344,7 +352,7 @@ def serve_arm(args):
         wait = t0 + sp["arrival_s"] - now
         if wait > 0:
             time.sleep(wait)
-        if warm_end is None and sp["arrival_s"] >= args.warm:
+        if warm_end is None and sp["arrival_s"] >= warm:
             hgf.hgf_serve_stats(srv, reset=True)
             warm_end = i
         st, rid = hgf.hgf_serve_submit(srv, req)
@@ -354,6 +362,18 @@ def serve_arm(args):
             hgf.hgf_serve_wait(srv, rid, 600000)
     stats = hgf.hgf_serve_stats(srv)
     hgf.hgf_serve_destroy(srv)
+    del pool
+    torch.cuda.empty_cache()
+    return stats
+
+
+def serve_arm(args):
+    """The serving run of run_serving at --rate for --duration seconds after --warm seconds."""
+    import torch
+    from paper_1803_00005_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    stats = run_serving(args.rate, args.duration, args.warm, args.slots)
     line = dict(metric="served HGF aggregate+WTA: p50/p99 latency and throughput",
                 value=stats["mpixel_labels_per_s"], unit=UNIT, n_gpus=1,
                 higher_is_better=True, impl="serve", data="synthetic",
@@ -454,22 +474,45 @@ def run_oracle(w, crop, reps):
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
+# The oracle's measured rate on the GPU machine's host (one core, 450x375 / L = 60 / n = 9), used only to
+# size the reference arm's sample so that its run stays within a few minutes.
+ORACLE_MPLS_ESTIMATE = 1.8
+REFERENCE_BUDGET_S = 210.0
+
+
+def reference_crop(w, steps_total):
+    """The whole image when (warm-up + timed) oracle steps on it fit the time budget at the
+    estimated rate, else the largest centred crop (same aspect) that does."""
+    full = w["width"] * w["height"] * w["n_labels"]
+    fit = REFERENCE_BUDGET_S * ORACLE_MPLS_ESTIMATE * 1e6 / max(1, steps_total)
+    if full <= fit:
+        return (w["width"], w["height"])
+    s = (fit / full) ** 0.5
+    return (max(8, int(w["width"] * s)), max(8, int(w["height"] * s)))
+
+
 def reference_arm(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    crop = (min(150, w["width"]), min(125, w["height"]))
+    crop = reference_crop(w, args.warmup + args.steps)
     res = run_oracle(w, crop, args.warmup + args.steps)
     t = res["times"][args.warmup:]
     total = sum(t)
     value = res["units"] * len(t) / total / 1e6
-    sample = (f"centred {crop[0]}x{crop[1]} crop of the {w['width']}x{w['height']} workload, all "
-              f"{w['n_labels']} labels, prepare + aggregate + WTA per step")
+    whole = crop == (w["width"], w["height"])
+    sample = ((f"the whole {w['width']}x{w['height']} workload" if whole else
+               f"centred {crop[0]}x{crop[1]} crop of the {w['width']}x{w['height']} workload") +
+              f", all {w['n_labels']} labels, prepare + aggregate + WTA per step, float64 numpy, "
+              f"one thread")
+    config = dict(workload=w["name"], parallelism="replicas x1",
+                  step="guidance precompute + aggregate + WTA", l2="n/a (CPU oracle)")
+    if not whole:
+        config["sample"] = sample
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
                 warmup=args.warmup, ms_per_step=1e3 * total / len(t), higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
-                impl="reference",
-                config=dict(workload=w["name"], sample=sample, l2="n/a (CPU)"),
+                impl="reference", config=config,
                 cpu_baseline=dict(value=value, unit=UNIT, cores=1, kind="oracle", sample=sample),
                 e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
@@ -524,6 +567,22 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------------- GPU arm
+def timed_leg(step, steps, flush, stream):
+    """Per-step device times (ms) of `steps` calls of step(), each bracketed by CUDA events on
+    `stream`, with the L2 flush written between steps (outside the events)."""
+    import torch
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush.fill_((i + 3) & 0xff)
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in zip(starts, ends)]
+
+
 def main():
     args = parse()
     w = WORKLOADS[args.workload]
@@ -633,7 +692,11 @@ def main():
     units = H * W * L * args.steps
     value = whole_job_value(units, world, t_max)
 
-    # roofline of the dominant kernel (largest share of the profiled time)
+    # roofline of the dominant kernel (largest share of the profiled time); the FP32 peak from
+    # the device's SM count and the SM clock sampled during the timed region
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+    fp32_peak = fp32_peak_tflops(sm_count, sm_mhz)
     kernels = {k: dict(launches=v["launches"], ms_per_step=v["ms"] / args.steps)
                for k, v in prof.items()}
     dom = max(prof.items(), key=lambda kv: kv[1]["ms"])[0] if prof else None
@@ -646,12 +709,53 @@ def main():
             launches_per_step = prof[dom]["launches"] / args.steps
             units_per_launch = (H * W * L if uname == "px*label" else H * W) / launches_per_step
             achieved = per_unit * units_per_launch / avg_s / 1e12
-            peak = FP64_PEAK_TFLOPS if dom == "k_inverse" else FP32_PEAK_TFLOPS
+            peak = FP64_PEAK_TFLOPS if dom == "k_inverse" else fp32_peak
             roof = dict(bound="alu", kernel=dom, achieved=achieved, peak=peak, unit="TFLOP/s",
                         frac=achieved / peak, traffic=profiled_traffic(dom, args.workload),
                         model=f"{per_unit:.0f} flops per {uname}",
                         peak_note=("nominal float64 rate" if dom == "k_inverse" else
-                                   "152 SMs x 128 FP32 lanes x 2 x 2070 MHz"))
+                                   f"derived: {sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 "
+                                   f"x {sm_mhz:.0f} MHz (median SM clock sampled under load)"))
+
+    # further legs on the same inputs (rank 0 of a single-GPU run): the aggregation alone with the
+    # guidance resident (warm; the precompute is timed separately per the metric's definition),
+    # the plain form's cold step, the single-pass kernel (cold and warm), a short served run
+    extra = {}
+    if rank == 0 and world == 1 and args.impl == "fused" and not args.no_extra:
+        flushes = flush
+        warm_ms = timed_leg(lambda: agg(ctx, g, cost, labels=labels), args.steps, flushes, stream)
+        prep_ms = timed_leg(lambda: hgf.hgf_guidance_update(ctx, g, img), args.steps, flushes,
+                            stream)
+        extra["warm"] = dict(value=H * W * L * len(warm_ms) / (sum(warm_ms) / 1e3) / 1e6,
+                             unit=UNIT, ms_per_step=statistics.mean(warm_ms),
+                             precompute_ms=statistics.mean(prep_ms),
+                             note="aggregate + WTA with the guidance moments and inverse "
+                                  "resident; precompute_ms: the guidance precompute alone")
+        np_steps = max(3, min(args.steps, 30))
+
+        def plain_step():
+            hgf.hgf_guidance_update(ctx, g, img)
+            hgf.hgf_aggregate_plain(ctx, g, cost, labels=labels)
+        plain_step()
+        plain_ms = timed_leg(plain_step, np_steps, flushes, stream)
+        plain_value = H * W * L * len(plain_ms) / (sum(plain_ms) / 1e3) / 1e6
+        extra["plain"] = dict(value=plain_value, unit=UNIT, ms_per_step=statistics.mean(plain_ms),
+                              steps=np_steps, fused_over_plain=value / plain_value,
+                              note="plain FP32 single-request GPU form: one kernel per step "
+                                   "(products, row sums, column sums, coefficients, output, WTA),"
+                                   " same step (precompute + aggregate + WTA)")
+        saved_kernel = args.kernel
+        hgf.hgf_set_tuning(ctx, kernel=1)
+        step()
+        sp_ms = timed_leg(step, args.steps, flushes, stream)
+        spw_ms = timed_leg(lambda: agg(ctx, g, cost, labels=labels), args.steps, flushes, stream)
+        hgf.hgf_set_tuning(ctx, kernel=saved_kernel)
+        extra["single_pass"] = dict(
+            value=H * W * L * len(sp_ms) / (sum(sp_ms) / 1e3) / 1e6, unit=UNIT,
+            ms_per_step=statistics.mean(sp_ms),
+            warm_value=H * W * L * len(spw_ms) / (sum(spw_ms) / 1e3) / 1e6,
+            note="hgf_tuning.kernel = 1: k_fused, slice moments to WTA in one persistent pass "
+                 "(same step; warm_value: aggregation alone)")
 
     # whole-step HBM fraction from the algorithmic bytes per px*label: the cost read once plus
     # the guidance image, inverse record and label write per pixel (amortised over L)
@@ -728,6 +832,17 @@ def main():
 
     hgf.hgf_guidance_release(g)
     hgf.hgf_destroy(ctx)
+    if rank == 0 and world == 1 and args.impl == "fused" and not args.no_extra:
+        del flush
+        torch.cuda.empty_cache()
+        st = run_serving(args.serve_rate, 3.0, 1.0, args.slots, device=local_rank)
+        extra["served"] = dict(
+            value=st["mpixel_labels_per_s"], unit=UNIT, p50_ms=st["p50_ms"], p99_ms=st["p99_ms"],
+            completed=st["completed"], rate_hz=args.serve_rate,
+            note=f"hgf_serve: Poisson {args.serve_rate:g} req/s for 3 s after 1 s warm-up; "
+                 "640x480..1920x1080, L 64..256, n in {3, 9, 19}, r in {4, 9}, bf16 costs, 30% "
+                 f"guidance reuse, 120 GiB budget, {args.slots} slots; latency from the "
+                 "scheduled arrival")
     if rank == 0:
         line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
                     warmup=args.warmup, ms_per_step=1e3 * t_max / args.steps,
@@ -742,7 +857,8 @@ def main():
                     stereo_pipeline=stereo_pipeline,
                     gpu_launches=int(launches),
                     clocks=clk, kernels=kernels, wall_s=wall,
-                    step_ms=dict(min=min(step_ms), median=statistics.median(step_ms)))
+                    step_ms=dict(min=min(step_ms), median=statistics.median(step_ms)),
+                    **extra)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
