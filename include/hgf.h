@@ -247,8 +247,13 @@ hgf_status hgf_autotune(hgf_ctx *ctx, const hgf_guidance *g, const void *cost, i
  * largest first, to balance the work). hgf_batch_run enqueues every job (guidance precompute +
  * fused aggregation + WTA) on those streams, forked from and joined back into `stream` by events:
  * it allocates nothing, so it can be captured into a CUDA graph; hgf_batch_launch_graph captures
- * it once into a graph (instantiated on the first call) and launches that graph. Job results are
- * the same as hgf_prepare + hgf_aggregate on each job alone.
+ * it once into a graph (instantiated on the first call) and launches that graph. When ctx is
+ * tuned to the single-pass kernel (hgf_tuning.kernel = 1) at hgf_batch_create, the jobs that
+ * kernel takes here (RGB guidance of degree 1 or 2, not compensated, r <= 24) are aggregated by
+ * one persistent launch per 40 jobs on `stream` after every precompute, the CTAs taking the
+ * jobs' (labels, strip, band) work items from one device counter; the other jobs take their
+ * streams. Job results are the same as hgf_prepare + hgf_aggregate on each job alone under the
+ * same tuning.
  * ------------------------------------------------------------------------------------------- */
 typedef struct hgf_batch hgf_batch;
 typedef struct {

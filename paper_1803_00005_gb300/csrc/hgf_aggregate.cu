@@ -271,6 +271,13 @@ cudaError_t launch_aggregate(const hgf_guidance *g, const void *cost, int cost_d
   return cudaGetLastError();
 }
 
+cudaError_t launch_wta_finalize(const unsigned long long *keys, int HW, int32_t *labels,
+                                float *best, cudaStream_t s, Profiler *prof) {
+  LaunchScope ls(prof, "k_wta_finalize", s);
+  k_wta_finalize<<<(HW + 255) / 256, 256, 0, s>>>(keys, nullptr, HW, labels, best, nullptr);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_wta(const float *filtered, int L, int H, int W, int32_t *labels, float *best,
                        cudaStream_t s, Profiler *prof, float *margin) {
   int HW = H * W;

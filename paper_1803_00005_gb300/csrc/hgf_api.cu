@@ -40,11 +40,15 @@ hgf_status cuda_fail(hgf_ctx *ctx, cudaError_t e, const char *where) {
                  cudaGetErrorString(e), in.c_str());
 }
 
-// Enters an API call on ctx: refuses work after a CUDA failure and makes the device current.
+// Enters an API call on ctx: refuses work after a CUDA failure, clears a non-sticky error that
+// an earlier call left on this thread (a sticky one comes back from the next call anyway) and
+// makes the device current.
 hgf_status enter(hgf_ctx *ctx) {
   if (!ctx) return HGF_EINVAL;
   if (ctx->sticky.load() != HGF_OK)
     return HGF_ECUDA;
+  cudaGetLastError();
+  failed_step() = nullptr;
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
   return HGF_OK;

@@ -194,7 +194,10 @@ class LaunchScope {
   LaunchScope(Profiler *p, const char *name, cudaStream_t s) : p_(p), name_(name), s_(s) {
     if (!p_) return;
     ++p_->launches;
-    if (p_->enabled) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    // no event pairs inside a graph capture (the capture check only when profiling)
+    if (p_->enabled && cudaStreamIsCapturing(s_, &cs) == cudaSuccess &&
+        cs == cudaStreamCaptureStatusNone) {
       a_ = p_->get();
       if (a_) cudaEventRecord(a_, s_);
     }
@@ -342,6 +345,30 @@ constexpr int kFusedCtasPerSm = 3;  // resident CTAs per SM its persistent grid 
 size_t onepass_smem(int n, int r);
 bool onepass_fits(const hgf_guidance *g);
 size_t onepass_ring_bytes(int n, int r, int ctas);
+// A job of a persistent batch launch of the single-pass kernel (hgf_onepass_batch.cu): its
+// guidance, cost, label count, filtered output (or NULL), its own WTA keys (H x W, reset by the
+// caller) and the nominal label count its bands are planned for.
+struct OnepassBatchJob {
+  const hgf_guidance *g;
+  const void *cost;
+  int cost_dtype, L;
+  float *filtered;
+  unsigned long long *keys;
+  int nominal;
+};
+// Whether g can join a batch launch (RGB monomials of degree 1 or 2, not compensated, within the
+// single-pass kernel's range), the ring floats one CTA needs for g, and the launch itself: one
+// persistent launch per 40 jobs on `s` (counters: one zeroed 64-bit work counter per launch).
+bool onepass_batch_eligible(const hgf_guidance *g);
+size_t onepass_batch_ring_floats(const hgf_guidance *g);
+cudaError_t launch_onepass_batch(const OnepassBatchJob *jobs, int n, float *ring_ws,
+                                 size_t ring_stride, int grid_ctas, int band_rows_tuned,
+                                 unsigned long long *counters, int *status, cudaStream_t s,
+                                 Profiler *prof);
+constexpr int kOnepassBatchJobsPerLaunch = 40;
+// Unpacks per-pixel WTA keys into labels / best (either may be NULL).
+cudaError_t launch_wta_finalize(const unsigned long long *keys, int HW, int32_t *labels,
+                                float *best, cudaStream_t s, Profiler *prof);
 // Tensor map of g's plane-major records: a box_w x 1 x record_floats(n) box (box_w = 0:
 // record_box_width(r)).
 cudaError_t make_record_map(const hgf_guidance *g, CUtensorMap *out, int box_w = 0);

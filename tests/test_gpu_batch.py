@@ -16,11 +16,16 @@ JOBS = [dict(w=320, h=240, L=32, seed=401, degree=2, r=9),
         dict(w=300, h=220, L=20, seed=406, degree=2, r=9, dtype="bf16")]
 
 
-def test_batch_equals_alone_direct_and_graph():
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_batch_equals_alone_direct_and_graph(kernel):
+    """kernel = 0: every job on the internal streams (two-kernel path); kernel = 1: the RGB
+    degree-1/2 jobs in one persistent single-pass launch, the others on the streams. Either way
+    each job equals the same job run alone under the same tuning, bit for bit."""
     torch = torch_cuda()
     from paper_1803_00005_gb300 import build, hgf, synth
     build.build()
     ctx = hgf.hgf_create(0)
+    hgf.hgf_set_tuning(ctx, kernel=kernel)
     items = []
     try:
         for sp in JOBS:
@@ -51,8 +56,14 @@ def test_batch_equals_alone_direct_and_graph():
                 for it in items:
                     it["out"][0].fill_(-1)
                     it["out"][1].fill_(float("nan"))
+                direct = runner is hgf.hgf_batch_run
+                hgf.hgf_profile_enable(ctx, direct)   # launches in a graph are not bracketed
                 runner(ctx, batch)
                 torch.cuda.synchronize()
+                hgf.hgf_profile_enable(ctx, False)
+                if direct:
+                    names = set(hgf.hgf_profile_report(ctx))
+                    assert ("k_fused_batch" in names) == (kernel == 1), names
                 for it in items:
                     assert np.array_equal(it["out"][0].cpu().numpy(), it["ref"][0])
                     assert np.array_equal(it["out"][1].cpu().numpy(), it["ref"][1])
