@@ -304,11 +304,22 @@ typedef struct {
   double mpixel_labels_per_s;              /* completed H*W*L / (last completion - first submit) */
   size_t budget_bytes, resident_bytes, peak_bytes;
   int slots, max_concurrent;               /* slots, most requests seen running at once */
+  /* where a completed request's time went: waiting in the queue (submit -> admission, mean and
+   * p99), and device time on its slot's stream, split by guidance size (index 0: n <= 3, 1:
+   * n <= 9, 2: n = 19): totals of the precompute (cache misses only) and of the aggregation +
+   * WTA in ms, and the completed requests of each class */
+  double queue_mean_ms, queue_p99_ms;
+  double prepare_ms_total[3], aggregate_ms_total[3];
+  uint64_t completed_by_class[3];
 } hgf_serve_stats_t;
 
 /* Create a server on `device` with a device-memory budget (slot workspaces + cached guidances),
  * `slots` concurrent streams (1..16) and a queue of at most `max_queue` waiting requests. Each
- * slot's workspace is allocated here for images up to max_pixels pixels and n <= max_n. */
+ * slot's workspace is allocated here for images up to max_pixels pixels and n <= max_n.
+ * Admission is in arrival order with one exception, by guidance degree: with two or more slots,
+ * requests with n = 19 (the longest, their float64 precompute alone taking several times that of
+ * n = 9) hold at most slots - 1 slots at once, and while the request at the head of the queue
+ * waits for that reason, a later request with n <= 9 (among the next 16) may start first. */
 hgf_status hgf_serve_create(int device, size_t budget_bytes, int slots, int max_queue,
                             int max_pixels, int max_n, hgf_server **out);
 /* Queue a request (the structure is copied; the buffers it points to must stay valid until the

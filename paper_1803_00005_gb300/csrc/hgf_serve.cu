@@ -61,7 +61,8 @@ struct Req {
   hgf_request r{};
   int n = 0;
   size_t guidance_bytes = 0;
-  Clock::time_point t_submit, t_done;
+  Clock::time_point t_submit, t_admit, t_done;
+  bool prepared_here = false;  // a cache miss: the slot ran the precompute
   std::atomic<int> finished{0};   // set by the host callback once the slot's work completed
   int state = Q_QUEUED;
   hgf_status status = HGF_EAGAIN;
@@ -74,7 +75,12 @@ struct Slot {
   cudaStream_t stream = nullptr;
   hgf_ctx *ctx = nullptr;  // owns this slot's prepare / coefficient / key workspaces
   Req *req = nullptr;
+  // timing events of the running request: start, precompute done, aggregation done
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
 };
+
+// Guidance-size class of the statistics: 0 for n <= 3, 1 for n <= 9, 2 above.
+int size_class(int n) { return n <= 3 ? 0 : n <= 9 ? 1 : 2; }
 
 size_t guidance_bytes_for(int C, int H, int W, int n, int r) {
   const size_t HW = (size_t)H * W;
@@ -102,7 +108,10 @@ struct hgf_server {
   // statistics
   uint64_t submitted = 0, completed = 0, failed = 0, rejected_busy = 0, rejected_nomem = 0;
   uint64_t hits = 0, misses = 0, evictions = 0;
-  std::vector<double> latencies;
+  std::vector<double> latencies, queue_waits;
+  double prep_ms[3] = {0, 0, 0}, agg_ms[3] = {0, 0, 0};
+  uint64_t done_by_class[3] = {0, 0, 0};
+  int running_big = 0;  // running requests with n = 19
   double units_done = 0.0;
   bool have_first = false;
   Clock::time_point first_submit, last_done;
@@ -151,12 +160,14 @@ struct hgf_server {
                  r.params.compensated, r.params.eps};
     auto it = cache.find(key);
     CacheEntry *e = nullptr;
-    cudaError_t err = cudaSuccess;
-    if (it != cache.end()) {
+    // the request's device time starts here (a failed record fails the request below)
+    cudaError_t err = cudaEventRecord(sl.ev[0], sl.stream);
+    q->prepared_here = false;
+    if (err == cudaSuccess && it != cache.end()) {
       e = it->second.get();
       ++hits;
       err = cudaStreamWaitEvent(sl.stream, e->ready, 0);
-    } else {
+    } else if (err == cudaSuccess) {
       if (!make_room(q->guidance_bytes)) {
         if (running == 0) {  // nothing in flight will free memory: it cannot run
           fail_request(q, HGF_ENOMEM);
@@ -204,12 +215,14 @@ struct hgf_server {
         err = launch_prepare(&g, r.img, sl.ctx->ws_prepare.ptr, sl.ctx->ws_prepare.size,
                              sl.stream, &sl.ctx->prof);
       if (err == cudaSuccess) err = cudaEventRecord(ent->ready, sl.stream);
+      q->prepared_here = true;
       cache_bytes += ent->bytes;
       peak = std::max(peak, resident());
       e = ent.get();
       cache[key] = std::move(ent);
     }
-    if (err == cudaSuccess) {
+    if (err == cudaSuccess) err = cudaEventRecord(sl.ev[1], sl.stream);
+    if (err == cudaSuccess && e) {
       hgf_tuning t = sl.ctx->tuning;
       AggregatePlan plan = plan_aggregate(&e->g, r.L, t, num_sms);
       const size_t per_label = coef_plane_floats(q->n, (size_t)r.H * r.W) * sizeof(float);
@@ -223,7 +236,13 @@ struct hgf_server {
                              (unsigned long long *)sl.ctx->ws_keys.ptr, plan, sl.stream,
                              &sl.ctx->prof);
     }
+    if (err == cudaSuccess) err = cudaEventRecord(sl.ev[2], sl.stream);
     if (err == cudaSuccess) err = cudaLaunchHostFunc(sl.stream, on_done, q);
+    if (!e) {
+      sticky = HGF_ECUDA;
+      fail_request(q, HGF_ECUDA);
+      return true;
+    }
     e->refs += 1;
     e->last_use = ++use_clock;
     q->entry = e;
@@ -235,10 +254,18 @@ struct hgf_server {
     }
     q->state = Q_RUNNING;
     q->slot = si;
+    q->t_admit = Clock::now();
     sl.req = q;
     ++running;
+    if (size_class(q->n) == 2) ++running_big;
     max_running = std::max(max_running, running);
     return true;
+  }
+
+  // An n = 19 request waits while n = 19 requests hold slots - 1 slots (two or more slots).
+  bool degree_blocked(const Req *q) const {
+    return size_class(q->n) == 2 && slots.size() >= 2 &&
+           running_big >= (int)slots.size() - 1;
   }
 
   void loop() {
@@ -252,6 +279,18 @@ struct hgf_server {
           q->status = HGF_OK;
           q->entry->refs -= 1;
           latencies.push_back(ms_between(q->t_submit, q->t_done));
+          queue_waits.push_back(ms_between(q->t_submit, q->t_admit));
+          const int cls = size_class(q->n);
+          float pm = 0.f, am = 0.f;
+          if (cudaEventElapsedTime(&pm, sl.ev[0], sl.ev[1]) != cudaSuccess ||
+              cudaEventElapsedTime(&am, sl.ev[1], sl.ev[2]) != cudaSuccess) {
+            cudaGetLastError();
+            pm = am = 0.f;
+          }
+          if (q->prepared_here) prep_ms[cls] += pm;
+          agg_ms[cls] += am;
+          ++done_by_class[cls];
+          if (cls == 2) --running_big;
           units_done += (double)q->r.H * q->r.W * q->r.L;
           last_done = std::max(last_done, q->t_done);
           ++completed;
@@ -260,7 +299,7 @@ struct hgf_server {
           cv_done.notify_all();
         }
       }
-      while (!queue.empty()) {  // admissions, in arrival order
+      while (!queue.empty()) {  // admissions, in arrival order (but see degree_blocked)
         int free_slot = -1;
         for (size_t i = 0; i < slots.size(); ++i)
           if (!slots[i].req) {
@@ -268,15 +307,23 @@ struct hgf_server {
             break;
           }
         if (free_slot < 0) break;
-        Req *q = queue.front();
+        auto pos = queue.begin();
+        if (sticky == HGF_OK && degree_blocked(*pos)) {
+          // the head waits for an n = 19 slot: a later request with n <= 9 may start first
+          auto alt = std::next(pos);
+          for (int k = 0; alt != queue.end() && k < 16 && size_class((*alt)->n) == 2; ++k) ++alt;
+          if (alt == queue.end() || size_class((*alt)->n) == 2) break;
+          pos = alt;
+        }
+        Req *q = *pos;
         if (sticky != HGF_OK) {
           fail_request(q, sticky);
-          queue.pop_front();
+          queue.erase(pos);
           cv_done.notify_all();
           continue;
         }
         if (!admit(q, free_slot)) break;
-        queue.pop_front();
+        queue.erase(pos);
         if (q->state == Q_FAILED) cv_done.notify_all();
       }
       if (stop && queue.empty() && running == 0) break;
@@ -302,6 +349,8 @@ hgf_status hgf_serve_create(int device, size_t budget_bytes, int slots, int max_
   s->max_n = max_n;
   auto cleanup = [&](hgf_status st) {
     for (auto &sl : s->slots) {
+      for (auto ev : sl.ev)
+        if (ev) cudaEventDestroy(ev);
       if (sl.stream) cudaStreamDestroy(sl.stream);
       hgf_destroy(sl.ctx);
     }
@@ -333,6 +382,8 @@ hgf_status hgf_serve_create(int device, size_t budget_bytes, int slots, int max_
     if (hgf_create(device, &sl.ctx) != HGF_OK) return cleanup(HGF_ECUDA);
     if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess)
       return cleanup(HGF_ECUDA);
+    for (auto &ev : sl.ev)
+      if (cudaEventCreate(&ev) != cudaSuccess) return cleanup(HGF_ECUDA);
     for (auto pr : {std::make_pair(&sl.ctx->ws_prepare, prep), std::make_pair(&sl.ctx->ws_coef, coef),
                     std::make_pair(&sl.ctx->ws_keys, keys)}) {
       if (cudaMalloc(&pr.first->ptr, pr.second) != cudaSuccess) {
@@ -462,10 +513,28 @@ hgf_status hgf_serve_stats(hgf_server *s, hgf_serve_stats_t *o, int reset) {
   o->peak_bytes = s->peak;
   o->slots = (int)s->slots.size();
   o->max_concurrent = s->max_running;
+  std::vector<double> qw = s->queue_waits;
+  if (!qw.empty()) {
+    std::sort(qw.begin(), qw.end());
+    double sum = 0;
+    for (double v : qw) sum += v;
+    o->queue_mean_ms = sum / qw.size();
+    o->queue_p99_ms = qw[std::min(qw.size() - 1, (size_t)std::ceil(0.99 * qw.size()) - 1)];
+  }
+  for (int c = 0; c < 3; ++c) {
+    o->prepare_ms_total[c] = s->prep_ms[c];
+    o->aggregate_ms_total[c] = s->agg_ms[c];
+    o->completed_by_class[c] = s->done_by_class[c];
+  }
   if (reset) {
     s->submitted = s->completed = s->failed = s->rejected_busy = s->rejected_nomem = 0;
     s->hits = s->misses = s->evictions = 0;
     s->latencies.clear();
+    s->queue_waits.clear();
+    for (int c = 0; c < 3; ++c) {
+      s->prep_ms[c] = s->agg_ms[c] = 0;
+      s->done_by_class[c] = 0;
+    }
     s->units_done = 0;
     s->have_first = false;
     s->max_running = s->running;
@@ -495,6 +564,8 @@ hgf_status hgf_serve_destroy(hgf_server *s) {
     if (kv.second->ready) cudaEventDestroy(kv.second->ready);
   }
   for (auto &sl : s->slots) {
+    for (auto ev : sl.ev)
+      if (ev) cudaEventDestroy(ev);
     if (sl.stream) cudaStreamDestroy(sl.stream);
     hgf_destroy(sl.ctx);
   }

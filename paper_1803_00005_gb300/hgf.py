@@ -90,10 +90,18 @@ class hgf_serve_stats_t(ctypes.Structure):
                [(n, ctypes.c_double) for n in ("p50_ms", "p99_ms", "mean_ms", "max_ms",
                                                "mpixel_labels_per_s")] + \
                [(n, ctypes.c_size_t) for n in ("budget_bytes", "resident_bytes", "peak_bytes")] + \
-               [("slots", ctypes.c_int), ("max_concurrent", ctypes.c_int)]
+               [("slots", ctypes.c_int), ("max_concurrent", ctypes.c_int)] + \
+               [("queue_mean_ms", ctypes.c_double), ("queue_p99_ms", ctypes.c_double),
+                ("prepare_ms_total", ctypes.c_double * 3),
+                ("aggregate_ms_total", ctypes.c_double * 3),
+                ("completed_by_class", ctypes.c_uint64 * 3)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        out = {}
+        for f, _ in self._fields_:
+            v = getattr(self, f)
+            out[f] = list(v) if isinstance(v, ctypes.Array) else v
+        return out
 
 
 _lib = None

@@ -201,3 +201,41 @@ def test_eviction_under_budget_keeps_results_exact():
         assert s["peak_bytes"] <= s["budget_bytes"]
     finally:
         hgf.hgf_serve_destroy(srv)
+
+
+def test_degree_aware_admission_and_breakdown():
+    """With two slots, requests with n = 19 hold one slot at most: a request with n = 3 queued
+    behind three n = 19 requests starts in the other slot at once and completes while the second
+    n = 19 request has not started. The statistics split each completed request's time into the
+    queue wait and its device time (precompute on a cache miss, aggregation), by guidance size."""
+    torch = torch_cuda()
+    from paper_1803_00005_gb300 import build, hgf
+    build.build()
+    big = [dict(w=640, h=480, L=64, seed=700 + i, degree=3, r=4, key=70 + i) for i in range(3)]
+    small = [dict(w=160, h=120, L=8, seed=710, degree=1, r=4, key=80)]
+    items = make_inputs(torch, big + small)
+    srv = hgf.hgf_serve_create(0, budget_bytes=16 << 30, slots=2, max_queue=16,
+                               max_pixels=640 * 480, max_n=19)
+    try:
+        ids = []
+        for it in items:
+            lab = torch.empty((it["h"], it["w"]), dtype=torch.int32, device="cuda")
+            it["lab"] = lab
+            req = hgf.make_request(it["key"], it["img"], it["cost"],
+                                   hgf.make_params(degree=it["degree"], r=it["r"], eps=1e-4), lab)
+            st, rid = hgf.hgf_serve_submit(srv, req)
+            assert st == hgf.HGF_OK
+            ids.append(rid)
+        assert hgf.hgf_serve_wait(srv, ids[3], 60000) == hgf.HGF_OK
+        assert hgf.hgf_serve_poll(srv, ids[1]) == hgf.HGF_EAGAIN   # waits for the n = 19 slot
+        for rid in ids:
+            assert hgf.hgf_serve_wait(srv, rid, 60000) == hgf.HGF_OK
+        s = hgf.hgf_serve_stats(srv)
+        assert s["completed"] == 4
+        assert list(s["completed_by_class"]) == [1, 0, 3]
+        assert s["prepare_ms_total"][2] > 0 and s["aggregate_ms_total"][2] > 0
+        assert s["aggregate_ms_total"][0] > 0
+        assert s["queue_p99_ms"] >= s["queue_mean_ms"] >= 0
+        assert s["max_concurrent"] == 2
+    finally:
+        hgf.hgf_serve_destroy(srv)
