@@ -26,6 +26,7 @@
 #include "hgf_stereo.cuh"
 #include "hgf_scan.cuh"
 #include "hgf_mbarrier.cuh"
+#include "hgf_f32x2.cuh"
 
 #include <algorithm>
 #include <type_traits>
@@ -225,8 +226,7 @@ __global__ void __launch_bounds__(NT, (coef_min_blocks<B, K, COMP>())) k_coef(co
             for (int i = 0; i < NG; ++i) kahan_add(V[k][i + 1], Vc[k][i + 1], -go[i] * p);
           } else {
             V[k][0] -= p;
-#pragma unroll
-            for (int i = 0; i < NG; ++i) V[k][i + 1] = fmaf(-go[i], p, V[k][i + 1]);
+            fma_channels<NG>(V[k], go, -p);  // fmaf(go, -p, .) == fmaf(-go, p, .)
           }
         }
       }
@@ -246,8 +246,7 @@ __global__ void __launch_bounds__(NT, (coef_min_blocks<B, K, COMP>())) k_coef(co
             for (int i = 0; i < NG; ++i) kahan_add(V[k][i + 1], Vc[k][i + 1], g[i] * p);
           } else {
             V[k][0] += p;
-#pragma unroll
-            for (int i = 0; i < NG; ++i) V[k][i + 1] = fmaf(g[i], p, V[k][i + 1]);
+            fma_channels<NG>(V[k], g, p);
           }
         }
       }
@@ -359,15 +358,40 @@ __global__ void __launch_bounds__(NT, (coef_min_blocks<B, K, COMP>())) k_coef(co
             a[kk][i] = 0.f;
           }
         }
+        if constexpr (KP == 2) {
+          // the pair's two mat-vecs as packed two-lane FMAs (the same roundings in the same order)
+          float2 a2[NG], c2[NG];
 #pragma unroll
-        for (int i = 0; i < NG; ++i) {
+          for (int i = 0; i < NG; ++i) {
+            c2[i] = make_float2(cov[0][i], cov[1][i]);
+            a2[i] = make_float2(0.f, 0.f);
+          }
 #pragma unroll
-          for (int j = i; j < NG; ++j) {
-            const float Mij = recv(NG + tri_index(NG, i, j));
+          for (int i = 0; i < NG; ++i) {
 #pragma unroll
-            for (int kk = 0; kk < KP; ++kk) {
-              a[kk][i] = fmaf(Mij, cov[kk][j], a[kk][i]);
-              if (j != i) a[kk][j] = fmaf(Mij, cov[kk][i], a[kk][j]);
+            for (int j = i; j < NG; ++j) {
+              const float Mij = recv(NG + tri_index(NG, i, j));
+              const float2 M2 = make_float2(Mij, Mij);
+              a2[i] = fma2(M2, c2[j], a2[i]);
+              if (j != i) a2[j] = fma2(M2, c2[i], a2[j]);
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < NG; ++i) {
+            a[0][i] = a2[i].x;
+            a[1][i] = a2[i].y;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < NG; ++i) {
+#pragma unroll
+            for (int j = i; j < NG; ++j) {
+              const float Mij = recv(NG + tri_index(NG, i, j));
+#pragma unroll
+              for (int kk = 0; kk < KP; ++kk) {
+                a[kk][i] = fmaf(Mij, cov[kk][j], a[kk][i]);
+                if (j != i) a[kk][j] = fmaf(Mij, cov[kk][i], a[kk][j]);
+              }
             }
           }
         }
@@ -475,6 +499,23 @@ __global__ void __launch_bounds__(NT) k_apply(const float *__restrict__ coef, in
     if constexpr (COMP) kahan_add(V[c], Vc[c], x);
     else V[c] += x;
   };
+  // V[c] += sign * x[c] for every channel; uncompensated: channel pairs as packed two-lane adds
+  // (x * -1 + V is exactly V - x), the same roundings as V[c] += sign * x[c]
+  auto acc_all = [&](const float *x, float sign) {
+    if constexpr (COMP) {
+#pragma unroll
+      for (int c = 0; c < C1; ++c) acc(c, sign * x[c]);
+    } else {
+      const float2 sg = make_float2(sign, sign);
+#pragma unroll
+      for (int c = 0; c + 1 < C1; c += 2) {
+        const float2 v = fma2(make_float2(x[c], x[c + 1]), sg, make_float2(V[c], V[c + 1]));
+        V[c] = v.x;
+        V[c + 1] = v.y;
+      }
+      if (C1 % 2) V[C1 - 1] = fmaf(x[C1 - 1], sign, V[C1 - 1]);
+    }
+  };
 
   // Same three-buffer rotation as k_coef; without the ring, the outgoing row (2r+1 rows back,
   // resident in L2) is prefetched two steps ahead as well.
@@ -507,14 +548,8 @@ __global__ void __launch_bounds__(NT) k_apply(const float *__restrict__ coef, in
           }
         }
       } else {
-        if (so >= add_lo) {
-#pragma unroll
-          for (int c = 0; c < C1; ++c) acc(c, -cur_o[c]);
-        }
-        if (s >= 0 && s < H) {
-#pragma unroll
-          for (int c = 0; c < C1; ++c) acc(c, cur[c]);
-        }
+        if (so >= add_lo) acc_all(cur_o, -1.f);
+        if (s >= 0 && s < H) acc_all(cur, 1.f);
       }
     }
     if (y2 < Y0) return;

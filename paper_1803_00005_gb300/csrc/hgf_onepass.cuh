@@ -229,8 +229,7 @@ __device__ __forceinline__ void fused_item(const FusedJob &jb, const CUtensorMap
             for (int i = 0; i < NG; ++i) acc1(k, i + 1, -go[i] * p);
           } else {
             V1[k][0] -= p;
-#pragma unroll
-            for (int i = 0; i < NG; ++i) V1[k][i + 1] = fmaf(-go[i], p, V1[k][i + 1]);
+            fma_channels<NG>(V1[k], go, -p);  // fmaf(go, -p, .) == fmaf(-go, p, .)
           }
         }
       }
@@ -246,8 +245,7 @@ __device__ __forceinline__ void fused_item(const FusedJob &jb, const CUtensorMap
             for (int i = 0; i < NG; ++i) acc1(k, i + 1, g[i] * p);
           } else {
             V1[k][0] += p;
-#pragma unroll
-            for (int i = 0; i < NG; ++i) V1[k][i + 1] = fmaf(g[i], p, V1[k][i + 1]);
+            fma_channels<NG>(V1[k], g, p);
           }
         }
       }
@@ -323,16 +321,42 @@ __device__ __forceinline__ void fused_item(const FusedJob &jb, const CUtensorMap
               cov[k][i] = fmaf(-m[i], pbar[k], mi);
             }
           }
+          if constexpr (K == 2) {
+            // the two labels' mat-vecs as packed two-lane FMAs (same roundings, same order)
+            float2 a2[NG], c2[NG];
 #pragma unroll
-          for (int i = 0; i < NG; ++i) {
-            const float *rr = opaque(rrow);
+            for (int i = 0; i < NG; ++i) {
+              c2[i] = make_float2(cov[0][i], cov[1][i]);
+              a2[i] = make_float2(0.f, 0.f);
+            }
 #pragma unroll
-            for (int j = i; j < NG; ++j) {
-              const float Mij = rr[(NG + tri_index(NG, i, j)) * BW];
+            for (int i = 0; i < NG; ++i) {
+              const float *rr = opaque(rrow);
 #pragma unroll
-              for (int k = 0; k < K; ++k) {
-                cf[k][i + 1] = fmaf(Mij, cov[k][j], cf[k][i + 1]);
-                if (j != i) cf[k][j + 1] = fmaf(Mij, cov[k][i], cf[k][j + 1]);
+              for (int j = i; j < NG; ++j) {
+                const float Mij = rr[(NG + tri_index(NG, i, j)) * BW];
+                const float2 M2 = make_float2(Mij, Mij);
+                a2[i] = fma2(M2, c2[j], a2[i]);
+                if (j != i) a2[j] = fma2(M2, c2[i], a2[j]);
+              }
+            }
+#pragma unroll
+            for (int i = 0; i < NG; ++i) {
+              cf[0][i + 1] = a2[i].x;
+              cf[1][i + 1] = a2[i].y;
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < NG; ++i) {
+              const float *rr = opaque(rrow);
+#pragma unroll
+              for (int j = i; j < NG; ++j) {
+                const float Mij = rr[(NG + tri_index(NG, i, j)) * BW];
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                  cf[k][i + 1] = fmaf(Mij, cov[k][j], cf[k][i + 1]);
+                  if (j != i) cf[k][j + 1] = fmaf(Mij, cov[k][i], cf[k][j + 1]);
+                }
               }
             }
           }
