@@ -109,6 +109,8 @@ def parse():
     ap.add_argument("--workload", choices=list(WORKLOADS), default="quarter")
     ap.add_argument("--kernel", type=int, choices=[0, 1, 2], default=0,
                     help="fused path: 0 automatic, 1 single-pass kernel, 2 two kernels")
+    ap.add_argument("--labels-per-pass", type=int, choices=[0, 1, 2, 4, 8], default=0,
+                    help="two-kernel path: labels per pass of the coefficient kernel (0 auto)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--inv-precision", choices=["f64", "df64", "f32"], default="f64",
                     help="arithmetic of the covariance assembly + inverse")
@@ -672,8 +674,8 @@ def main():
                              inv_precision=args.inv_precision)
     g = hgf.hgf_prepare(ctx, img, params)
     agg = hgf.hgf_aggregate_plain if args.impl == "plain" else hgf.hgf_aggregate
-    if args.kernel:
-        hgf.hgf_set_tuning(ctx, kernel=args.kernel)
+    if args.kernel or args.labels_per_pass:
+        hgf.hgf_set_tuning(ctx, kernel=args.kernel, labels_per_pass=args.labels_per_pass)
 
     def step():
         hgf.hgf_guidance_update(ctx, g, img)
@@ -704,6 +706,8 @@ def main():
     wall = time.perf_counter() - wall0
     hgf.hgf_profile_enable(ctx, False)
     launches = hgf.hgf_launch_count(ctx) - launches0
+    main_path = {1: "single pass (k_fused)", 2: "two kernels (k_coef + k_apply)",
+                 3: "plain form"}.get(hgf.hgf_last_plan(ctx)["path"], "?")
     prof = hgf.hgf_profile_report(ctx)
     clk = clocks.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
@@ -765,17 +769,21 @@ def main():
                                    "(products, row sums, column sums, coefficients, output, WTA),"
                                    " same step (precompute + aggregate + WTA)")
         saved_kernel = args.kernel
-        hgf.hgf_set_tuning(ctx, kernel=1)
-        step()
-        sp_ms = timed_leg(step, args.steps, flushes, stream)
-        spw_ms = timed_leg(lambda: agg(ctx, g, cost, labels=labels), args.steps, flushes, stream)
+        notes = {1: "hgf_tuning.kernel = 1: k_fused, slice moments to WTA in one persistent pass",
+                 2: "hgf_tuning.kernel = 2: k_coef (coefficients to a workspace) + k_apply "
+                    "(their box filter, output, WTA)"}
+        for kern, key in ((1, "single_pass"), (2, "two_kernel")):
+            hgf.hgf_set_tuning(ctx, kernel=kern)
+            step()
+            sp_ms = timed_leg(step, args.steps, flushes, stream)
+            spw_ms = timed_leg(lambda: agg(ctx, g, cost, labels=labels), args.steps, flushes,
+                               stream)
+            extra[key] = dict(
+                value=H * W * L * len(sp_ms) / (sum(sp_ms) / 1e3) / 1e6, unit=UNIT,
+                ms_per_step=statistics.mean(sp_ms),
+                warm_value=H * W * L * len(spw_ms) / (sum(spw_ms) / 1e3) / 1e6,
+                note=notes[kern] + " (same step; warm_value: aggregation alone)")
         hgf.hgf_set_tuning(ctx, kernel=saved_kernel)
-        extra["single_pass"] = dict(
-            value=H * W * L * len(sp_ms) / (sum(sp_ms) / 1e3) / 1e6, unit=UNIT,
-            ms_per_step=statistics.mean(sp_ms),
-            warm_value=H * W * L * len(spw_ms) / (sum(spw_ms) / 1e3) / 1e6,
-            note="hgf_tuning.kernel = 1: k_fused, slice moments to WTA in one persistent pass "
-                 "(same step; warm_value: aggregation alone)")
 
     # whole-step HBM fraction from the algorithmic bytes per px*label: the cost read once plus
     # the guidance image, inverse record and label write per pixel (amortised over L)
@@ -872,7 +880,7 @@ def main():
                     impl=args.impl,
                     config=dict(workload=w["name"], parallelism=f"replicas x{world}",
                                 l2="256 MiB buffer written between timed steps",
-                                step="guidance precompute + aggregate + WTA"),
+                                step="guidance precompute + aggregate + WTA", path=main_path),
                     roofline=roof, hbm=hbm, cpu_baseline=cpu,
                     cpu_baseline_all_cores=cpu_all, e2e=e2e, e2e_stereo=e2e_stereo,
                     stereo_pipeline=stereo_pipeline,

@@ -130,9 +130,9 @@ hgf_status hgf_guidance_export(hgf_ctx *ctx, const hgf_guidance *g, float *minv_
 /* Fused aggregation + WTA (Sec. 1 pipeline; Eqs. GF_w / HGF_z1): for every label slice p of the
  * cost volume, pbar = A(p), cov_i = A(G_i p) - mu_i pbar, a = (Sigma + eps E)^-1 cov,
  * b = pbar - a.mu, q = sum_i A(a_i) G_i + A(b); then labels = argmin_l q_l (lowest l on ties,
- * NaN counted as +inf) and best = min_l q_l. By default two kernels per chunk of labels with a
- * coefficient workspace in between; for n <= 9 (r <= 24) hgf_tuning.kernel = 1 selects one
- * kernel that does all of it, WTA included, in a single pass over the slices. For a guidance prepared with HGF_FORM_PAPER the
+ * NaN counted as +inf) and best = min_l q_l. Either one kernel does all of it, WTA included, in a
+ * single pass over the slices (n <= 9, r <= 24), or two kernels per chunk of labels with a
+ * coefficient workspace in between (see hgf_tuning.kernel for which the plan takes). For a guidance prepared with HGF_FORM_PAPER the
  * coefficients are those of the paper's form instead: w = (lambda E + Gram)^-1 B([1, G] p) and
  * q = sum_i A(w_i) G_i + A(w_0) (see hgf_form).
  * cost: device, L x H x W of cost_dtype (HGF_F32, HGF_BF16 or HGF_F16), H, W of the guidance.
@@ -212,8 +212,10 @@ hgf_status hgf_filter_host(hgf_ctx *ctx, const float *img, int C, int H, int W,
  * and which kernels run: kernel = 1 the single-pass kernel (slice moments, coefficients, their
  * box filter, output and WTA of two labels at a time in one pass over the slices, with a small
  * L2-resident ring of coefficient window sums instead of a coefficient workspace; n <= 9 and
- * r <= 24), 2 (or 0, automatic) the two-kernel path (coefficients to a workspace, then output +
- * WTA: the only one for n = 19). labels_per_pass, chunk_labels and apply_mode apply to
+ * r <= 24), 2 the two-kernel path (coefficients to a workspace, then output + WTA: the only one
+ * for n = 19), 0 automatic: the single pass where it applies, its output strips (128 - 4r
+ * columns) need no more strips than the two-kernel path's (128 - 2r) and H * W * L is at least
+ * 8e6, the two-kernel path otherwise. labels_per_pass, chunk_labels and apply_mode apply to
  * the two-kernel path only. Returns HGF_EINVAL for values the kernels cannot take. */
 typedef struct {
   int labels_per_pass;

@@ -201,7 +201,8 @@ AggregatePlan plan_aggregate(const hgf_guidance *g, int L, const hgf_tuning &t, 
   p.nominal = std::max(2, std::min(64, (L + 1) / 2 * 2));
   if (t.labels_per_pass == 2 ||
       ((t.labels_per_pass == 4 || t.labels_per_pass == 8) &&
-       coef_smem(g->n, g->C, t.labels_per_pass, g->r) <= 227 * 1024))
+       coef_smem(g->n, g->C, t.labels_per_pass, g->r) <= 227 * 1024) ||
+      (t.labels_per_pass == 1 && !records_staged(g->n)))
     p.K = t.labels_per_pass;
   const size_t plane = coef_plane_floats(g->n, (size_t)g->H * g->W) * sizeof(float);
   // labels per chunk: all labels while the coefficient workspace stays under 4 GiB
@@ -219,11 +220,17 @@ AggregatePlan plan_aggregate(const hgf_guidance *g, int L, const hgf_tuning &t, 
   (void)passes;
   (void)num_sms;
   p.band_rows = t.band_rows;  // 0: each kernel picks its bands from its occupancy at launch
-  // the two-kernel path unless tuned to the single-pass kernel (within its range): measured on
-  // GB300 the two are level at 450x375 / L = 60 / n = 9 / r = 9 (0.54 ms each) and the two-kernel
-  // path is ahead at 1400x1100 / L = 256 (18.0 vs 21.4 ms), where the single pass's narrower
-  // output strips (128 - 4r columns against 128 - 2r) cost more than its saved workspace traffic
-  p.onepass = t.kernel == 1 && onepass_fits(g);
+  // kernel path: as tuned, else the single pass when its narrower output strips (128 - 4r columns
+  // against the two-kernel path's 128 - 2r) cost no extra strips and the job fills the GPU. On
+  // GB300 (warm aggregation, 15 shapes): with equal strip counts the single pass was 1-5 %
+  // faster from 8 Mpixel*labels up (450x375/L=60/n=9/r=9: 0.535 vs 0.539 ms; 640x480/L=64/n=3:
+  // 0.49 vs 0.52 ms) and 5 % slower below (320x240/L=32); with more strips it was 3-40 % slower
+  // (1400x1100/L=256/r=9: 16 vs 13 strips, 20.6 vs 17.9 ms)
+  const int strips_single = (g->W + NT - 4 * g->r - 1) / std::max(1, NT - 4 * g->r);
+  const int strips_two = (g->W + NT - 2 * g->r - 1) / std::max(1, NT - 2 * g->r);
+  const bool auto_single = strips_single == strips_two &&
+                           (double)g->H * g->W * L >= 8.0e6;
+  p.onepass = onepass_fits(g) && (t.kernel == 1 || (t.kernel == 0 && auto_single));
   p.onepass_ctas = std::max(1, num_sms) * kFusedCtasPerSm;
   return p;
 }

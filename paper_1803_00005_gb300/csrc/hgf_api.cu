@@ -394,9 +394,9 @@ hgf_status hgf_guidance_export(hgf_ctx *ctx, const hgf_guidance *g, float *minv_
 
 hgf_status hgf_set_tuning(hgf_ctx *ctx, const hgf_tuning *t) {
   if (!ctx || !t) return HGF_EINVAL;
-  if (t->labels_per_pass != 0 && t->labels_per_pass != 2 && t->labels_per_pass != 4 &&
-      t->labels_per_pass != 8)
-    return set_err(ctx, HGF_EINVAL, "labels_per_pass must be 0, 2, 4 or 8");
+  if (t->labels_per_pass != 0 && t->labels_per_pass != 1 && t->labels_per_pass != 2 &&
+      t->labels_per_pass != 4 && t->labels_per_pass != 8)
+    return set_err(ctx, HGF_EINVAL, "labels_per_pass must be 0, 1, 2, 4 or 8");
   if (t->band_rows < 0 || t->chunk_labels < 0)
     return set_err(ctx, HGF_EINVAL, "band_rows and chunk_labels must be >= 0");
   if (t->apply_mode < 0 || t->apply_mode > 2)

@@ -56,7 +56,7 @@ __host__ __device__ constexpr bool stage_records() { return records_staged(basis
 // labels per pass, two at four), passed to __launch_bounds__ as the register budget
 template <int B, int K, bool COMP>
 __host__ __device__ constexpr int coef_min_blocks() {
-  return !stage_records<B>() ? 1
+  return !stage_records<B>() ? (K == 1 ? 3 : 1)  // n = 19: one label per pass leaves room for 3
          : (K <= 2 && !COMP) ? (kRecordBuffers == 1 ? 4 : 3)
          : K <= 4 ? 2 : 1;
 }
@@ -226,7 +226,12 @@ __global__ void __launch_bounds__(NT, (coef_min_blocks<B, K, COMP>())) k_coef(co
             for (int i = 0; i < NG; ++i) kahan_add(V[k][i + 1], Vc[k][i + 1], -go[i] * p);
           } else {
             V[k][0] -= p;
-            fma_channels<NG>(V[k], go, -p);  // fmaf(go, -p, .) == fmaf(-go, p, .)
+            if constexpr (STAGE) {
+              fma_channels<NG>(V[k], go, -p);  // fmaf(go, -p, .) == fmaf(-go, p, .)
+            } else {
+#pragma unroll
+              for (int i = 0; i < NG; ++i) V[k][i + 1] = fmaf(-go[i], p, V[k][i + 1]);
+            }
           }
         }
       }
@@ -246,7 +251,12 @@ __global__ void __launch_bounds__(NT, (coef_min_blocks<B, K, COMP>())) k_coef(co
             for (int i = 0; i < NG; ++i) kahan_add(V[k][i + 1], Vc[k][i + 1], g[i] * p);
           } else {
             V[k][0] += p;
-            fma_channels<NG>(V[k], g, p);
+            if constexpr (STAGE) {
+              fma_channels<NG>(V[k], g, p);
+            } else {
+#pragma unroll
+              for (int i = 0; i < NG; ++i) V[k][i + 1] = fmaf(g[i], p, V[k][i + 1]);
+            }
           }
         }
       }
@@ -358,8 +368,9 @@ __global__ void __launch_bounds__(NT, (coef_min_blocks<B, K, COMP>())) k_coef(co
             a[kk][i] = 0.f;
           }
         }
-        if constexpr (KP == 2) {
-          // the pair's two mat-vecs as packed two-lane FMAs (the same roundings in the same order)
+        if constexpr (KP == 2 && STAGE) {
+          // the pair's two mat-vecs as packed two-lane FMAs (the same roundings in the same order;
+          // measured slower at n = 19, whose records are read from L2, so kept to n <= 9)
           float2 a2[NG], c2[NG];
 #pragma unroll
           for (int i = 0; i < NG; ++i) {
@@ -752,7 +763,15 @@ cudaError_t launch_basis(const hgf_guidance *g, const void *cost, int cost_dtype
       e = launch_chunk<B, 2, true>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys,
                                    keys2, p.band_rows, false, p.nominal, status, stereo, map, s,
                                    prof);
-    else if (p.K == 4)
+    else if (p.K == 1) {
+      // one label per pass: built for the bases whose records are not staged (n = 19)
+      if constexpr (!stage_records<B>())
+        e = launch_chunk<B, 1, false>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys,
+                                      keys2, p.band_rows, p.apply_ring, p.nominal, status, stereo,
+                                      map, s, prof);
+      else
+        e = cudaErrorInvalidValue;
+    } else if (p.K == 4)
       e = launch_chunk<B, 4, false>(g, cost, cost_dtype, l0, nc, filtered, coef_ws, keys, keys2,
                                     p.band_rows, p.apply_ring, p.nominal, status, stereo, map, s,
                                     prof);

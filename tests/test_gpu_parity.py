@@ -200,7 +200,7 @@ def test_quarter_size_n9_regions(ctx, path):
     c = synth.CONFIG_QUARTER
     case = synth.make_case(c["width"], c["height"], c["n_labels"], c["seed"], "f32")
     q, labels, best = run_path(ctx, case.guidance, case.cost, "f32", c["degree"], c["r"], c["eps"],
-                               kernel=1 if path == "single-pass" else 0)
+                               kernel=1 if path == "single-pass" else 2)
     plan = hgf.hgf_last_plan(ctx)
     assert plan["path"] == (1 if path == "single-pass" else 2)
     H, W = c["height"], c["width"]
@@ -261,6 +261,24 @@ def test_results_independent_of_label_chunking(ctx):
             assert np.array_equal(got[0], base[0]) and np.array_equal(got[1], base[1])
     finally:
         hgf.hgf_set_tuning(ctx)
+
+
+def test_n19_labels_per_pass_bit_identical(ctx):
+    """n = 19 with one label per pass of the coefficient kernel (three CTAs per SM instead of
+    two) gives the same bits as two labels per pass, and matches the oracle."""
+    from paper_1803_00005_gb300 import hgf
+    case, ref = oracle_case(150, 80, 5, 33, degree=3, r=4, eps=1e-4)
+    hgf.hgf_set_tuning(ctx, labels_per_pass=2, kernel=2)
+    try:
+        a = run_path(ctx, case.guidance, case.cost, "f32", 3, 4, 1e-4)
+        hgf.hgf_set_tuning(ctx, labels_per_pass=1, kernel=2)
+        b = run_path(ctx, case.guidance, case.cost, "f32", 3, 4, 1e-4)
+        assert hgf.hgf_last_plan(ctx)["labels_per_pass"] == 1
+    finally:
+        hgf.hgf_set_tuning(ctx)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    check_against_oracle(*b, ref)
 
 
 @pytest.mark.parametrize("degree,r", [(2, 9), (1, 4), (3, 4)])

@@ -49,16 +49,17 @@ def test_static_scratch_matches_allocating_path():
         hgf.hgf_guidance_release(g)
         hgf.hgf_set_tuning(ctx)
 
-        # two-kernel path (the default): 900 x 700 at n = 9 takes 25.2 MB of coefficient planes
-        # per label, so the 64 MiB array holds two labels' planes next to the keys and 7 labels
-        # run in 4 chunks
+        # two-kernel path: 900 x 700 at n = 9 takes 25.2 MB of coefficient planes per label, so
+        # the 64 MiB array holds two labels' planes next to the keys and 7 labels run in 4 chunks
         case = synth.make_case(900, 700, 7, 78, "f32")
         L, H, W = case.cost.shape
         img = torch.from_numpy(case.guidance).cuda()
         cost = torch.from_numpy(case.cost).cuda()
+        hgf.hgf_set_tuning(ctx, kernel=2)
         g = hgf.hgf_prepare(ctx, img, hgf.make_params(degree=2, r=9, eps=1e-4))
         _compare(torch, hgf, ctx, g, cost, L, H, W)
         hgf.hgf_guidance_release(g)
+        hgf.hgf_set_tuning(ctx)
 
         # more pixels than the array holds keys and planes for: refused
         big = torch.rand((1, 3000, 3000), device="cuda")
