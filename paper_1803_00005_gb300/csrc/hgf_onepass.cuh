@@ -308,25 +308,25 @@ __device__ __forceinline__ void fused_item(const FusedJob &jb, const CUtensorMap
         } else {
           const float invN =
               1.f / (float)(clipped_count(xi, r, W) * clipped_count(y1, r, H));
-          float m[NG], cov[K][NG], pbar[K];
+          float m[NG];
 #pragma unroll
           for (int i = 0; i < NG; ++i) m[i] = rrow[i * BW];
-#pragma unroll
-          for (int k = 0; k < K; ++k) {
-            const float *row = S1 + k * C1 * kRowStride;
-            pbar[k] = window(row, t - r, r) * invN;
-#pragma unroll
-            for (int i = 0; i < NG; ++i) {
-              const float mi = window(row + (i + 1) * kRowStride, t - r, r) * invN;
-              cov[k][i] = fmaf(-m[i], pbar[k], mi);
-            }
-          }
-          if constexpr (K == 2) {
-            // the two labels' mat-vecs as packed two-lane FMAs (same roundings, same order)
+          if constexpr (K == 2 && !COMP) {
+            // the two labels in packed two-lane arithmetic: window sums, means, cov, the mat-vec
+            // and b, with the same roundings in the same order as the scalar branch below
+            // (fmaf(-a, m, b) == fmaf(a, -m, b))
+            const float2 iN2 = make_float2(invN, invN);
+            const float *r0 = S1, *r1 = S1 + C1 * kRowStride;
+            const int ia = 4 + (t - r) + 2 * r, ib = 3 + (t - r);
+            auto win2 = [&](int c) {
+              return sub2(make_float2(r0[c * kRowStride + ia], r1[c * kRowStride + ia]),
+                          make_float2(r0[c * kRowStride + ib], r1[c * kRowStride + ib]));
+            };
+            const float2 pb2 = mul2(win2(0), iN2);
             float2 a2[NG], c2[NG];
 #pragma unroll
             for (int i = 0; i < NG; ++i) {
-              c2[i] = make_float2(cov[0][i], cov[1][i]);
+              c2[i] = fma2(make_float2(-m[i], -m[i]), pb2, mul2(win2(i + 1), iN2));
               a2[i] = make_float2(0.f, 0.f);
             }
 #pragma unroll
@@ -340,12 +340,27 @@ __device__ __forceinline__ void fused_item(const FusedJob &jb, const CUtensorMap
                 if (j != i) a2[j] = fma2(M2, c2[i], a2[j]);
               }
             }
+            float2 b2 = pb2;
 #pragma unroll
             for (int i = 0; i < NG; ++i) {
+              b2 = fma2(a2[i], make_float2(-m[i], -m[i]), b2);
               cf[0][i + 1] = a2[i].x;
               cf[1][i + 1] = a2[i].y;
             }
+            cf[0][0] = b2.x;
+            cf[1][0] = b2.y;
           } else {
+            float cov[K][NG], pbar[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+              const float *row = S1 + k * C1 * kRowStride;
+              pbar[k] = window(row, t - r, r) * invN;
+#pragma unroll
+              for (int i = 0; i < NG; ++i) {
+                const float mi = window(row + (i + 1) * kRowStride, t - r, r) * invN;
+                cov[k][i] = fmaf(-m[i], pbar[k], mi);
+              }
+            }
 #pragma unroll
             for (int i = 0; i < NG; ++i) {
               const float *rr = opaque(rrow);
@@ -359,13 +374,13 @@ __device__ __forceinline__ void fused_item(const FusedJob &jb, const CUtensorMap
                 }
               }
             }
-          }
 #pragma unroll
-          for (int k = 0; k < K; ++k) {
-            float b = pbar[k];
+            for (int k = 0; k < K; ++k) {
+              float b = pbar[k];
 #pragma unroll
-            for (int i = 0; i < NG; ++i) b = fmaf(-cf[k][i + 1], m[i], b);
-            cf[k][0] = b;
+              for (int i = 0; i < NG; ++i) b = fmaf(-cf[k][i + 1], m[i], b);
+              cf[k][0] = b;
+            }
           }
         }
       }
