@@ -678,8 +678,12 @@ def main():
         hgf.hgf_set_tuning(ctx, kernel=args.kernel, labels_per_pass=args.labels_per_pass)
 
     def step():
-        hgf.hgf_guidance_update(ctx, g, img)
-        agg(ctx, g, cost, labels=labels)
+        # one frame: guidance precompute + aggregation + WTA (hgf_filter: both in one call)
+        if args.impl == "plain":
+            hgf.hgf_guidance_update(ctx, g, img)
+            agg(ctx, g, cost, labels=labels)
+        else:
+            hgf.hgf_filter(ctx, g, img, cost, labels=labels)
 
     for i in range(args.warmup):
         flush.fill_(i & 0xff)
@@ -880,7 +884,9 @@ def main():
                     impl=args.impl,
                     config=dict(workload=w["name"], parallelism=f"replicas x{world}",
                                 l2="256 MiB buffer written between timed steps",
-                                step="guidance precompute + aggregate + WTA", path=main_path),
+                                step="guidance precompute + aggregate + WTA"
+                                     + ("" if args.impl == "plain" else " (one hgf_filter call)"),
+                                path=main_path),
                     roofline=roof, hbm=hbm, cpu_baseline=cpu,
                     cpu_baseline_all_cores=cpu_all, e2e=e2e, e2e_stereo=e2e_stereo,
                     stereo_pipeline=stereo_pipeline,

@@ -143,6 +143,15 @@ hgf_status hgf_aggregate(hgf_ctx *ctx, const hgf_guidance *g, const void *cost, 
                          int L, void *filtered, int filtered_dtype, int32_t *labels, float *best,
                          void *stream);
 
+/* One frame in one call: hgf_guidance_update(g, img) (Secs. 5.1 and 3: guidance, moments,
+ * inverse) followed by hgf_aggregate(g, cost) (aggregation and WTA) on the same stream, with the
+ * results of those two calls; g is updated in place and stays usable after it. img: device,
+ * C x H x W float32 of the guidance's shape; the other arguments as for hgf_aggregate. Errors as
+ * for the two calls. */
+hgf_status hgf_filter(hgf_ctx *ctx, hgf_guidance *g, const float *img, const void *cost,
+                      int cost_dtype, int L, void *filtered, int filtered_dtype, int32_t *labels,
+                      float *best, void *stream);
+
 /* hgf_aggregate for callers that cannot allocate device memory while they run: fixed-latency loops
  * (cudaMalloc/cudaFree can synchronise the device and block), or plugins in a program that hands
  * out all device memory from its own allocator at start-up, where a late cudaMalloc fails or
@@ -213,9 +222,9 @@ hgf_status hgf_filter_host(hgf_ctx *ctx, const float *img, int C, int H, int W,
  * box filter, output and WTA of two labels at a time in one pass over the slices, with a small
  * L2-resident ring of coefficient window sums instead of a coefficient workspace; n <= 9 and
  * r <= 24), 2 the two-kernel path (coefficients to a workspace, then output + WTA: the only one
- * for n = 19), 0 automatic: the single pass where it applies, its output strips (128 - 4r
- * columns) need no more strips than the two-kernel path's (128 - 2r) and H * W * L is at least
- * 8e6, the two-kernel path otherwise. labels_per_pass, chunk_labels and apply_mode apply to
+ * for n = 19), 0 automatic: the single pass where it applies and either n <= 3 or its output
+ * strips (128 - 4r columns) need no more strips than the two-kernel path's (128 - 2r) and
+ * H * W * L is at least 8e6, the two-kernel path otherwise. labels_per_pass, chunk_labels and apply_mode apply to
  * the two-kernel path only. Returns HGF_EINVAL for values the kernels cannot take. */
 typedef struct {
   int labels_per_pass;

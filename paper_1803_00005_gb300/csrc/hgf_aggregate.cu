@@ -220,18 +220,20 @@ AggregatePlan plan_aggregate(const hgf_guidance *g, int L, const hgf_tuning &t, 
   (void)passes;
   (void)num_sms;
   p.band_rows = t.band_rows;  // 0: each kernel picks its bands from its occupancy at launch
-  // kernel path: as tuned, else the single pass when its narrower output strips (128 - 4r columns
-  // against the two-kernel path's 128 - 2r) cost no extra strips and the job fills the GPU. On
-  // GB300 (warm aggregation, 15 shapes): with equal strip counts the single pass was 1-5 %
-  // faster from 8 Mpixel*labels up (450x375/L=60/n=9/r=9: 0.535 vs 0.539 ms; 640x480/L=64/n=3:
-  // 0.49 vs 0.52 ms) and 5 % slower below (320x240/L=32); with more strips it was 3-40 % slower
-  // (1400x1100/L=256/r=9: 16 vs 13 strips, 20.6 vs 17.9 ms)
+  // kernel path: as tuned, else for n <= 3 the single pass (four CTAs an SM), and for larger n
+  // the single pass when its narrower output strips (128 - 4r columns against the two-kernel
+  // path's 128 - 2r) cost no extra strips and the job fills the GPU. On GB300 (warm aggregation,
+  // 15 shapes): at n = 3 the single pass was 1-17 % faster on all five shapes, also with more
+  // strips (450x375/L=60/r=4: 0.253 vs 0.263 ms with 5 against 4 strips; 640x480/L=64/r=4:
+  // 0.409 vs 0.519 ms; 320x240/L=32: 0.082 vs 0.085 ms); at n = 9 with equal strip counts it
+  // was 1-5 % faster from 8 Mpixel*labels up (450x375/L=60/r=9: 0.531 vs 0.541 ms) and with more
+  // strips 3-40 % slower (1400x1100/L=256/r=9: 16 vs 13 strips, 20.4 vs 17.9 ms)
   const int strips_single = (g->W + NT - 4 * g->r - 1) / std::max(1, NT - 4 * g->r);
   const int strips_two = (g->W + NT - 2 * g->r - 1) / std::max(1, NT - 2 * g->r);
-  const bool auto_single = strips_single == strips_two &&
-                           (double)g->H * g->W * L >= 8.0e6;
+  const bool auto_single = g->n <= 3 || (strips_single == strips_two &&
+                                         (double)g->H * g->W * L >= 8.0e6);
   p.onepass = onepass_fits(g) && (t.kernel == 1 || (t.kernel == 0 && auto_single));
-  p.onepass_ctas = std::max(1, num_sms) * kFusedCtasPerSm;
+  p.onepass_ctas = std::max(1, num_sms) * fused_ctas_per_sm(g->n);
   return p;
 }
 

@@ -238,6 +238,21 @@ hgf_status aggregate_locked(hgf_ctx *ctx, const hgf_guidance *g, const void *cos
   return HGF_OK;
 }
 
+// hgf_guidance_update + hgf_aggregate with ctx->mu held and arguments checked; the aggregation
+// waits for `before_aggregate` when given (hgf_filter_host: the cost upload, which then overlaps
+// the guidance precompute).
+hgf_status filter_locked(hgf_ctx *ctx, hgf_guidance *g, const float *img, const void *cost,
+                         int cost_dtype, int L, void *filtered, int32_t *labels, float *best,
+                         cudaStream_t s, cudaEvent_t before_aggregate = nullptr) {
+  hgf_status st = prepare_locked(ctx, g, img, s);
+  if (st != HGF_OK) return st;
+  if (before_aggregate) {
+    cudaError_t e = cudaStreamWaitEvent(s, before_aggregate, 0);
+    if (e != cudaSuccess) return cuda_fail_locked(ctx, e, "hgf_filter wait");
+  }
+  return aggregate_locked(ctx, g, cost, cost_dtype, L, filtered, labels, best, s);
+}
+
 }  // namespace
 
 namespace hgf {
@@ -492,6 +507,20 @@ hgf_status hgf_aggregate(hgf_ctx *ctx, const hgf_guidance *g, const void *cost, 
                           (cudaStream_t)stream);
 }
 
+hgf_status hgf_filter(hgf_ctx *ctx, hgf_guidance *g, const float *img, const void *cost,
+                      int cost_dtype, int L, void *filtered, int filtered_dtype, int32_t *labels,
+                      float *best, void *stream) {
+  NvtxRange nvtx_range("hgf_filter");
+  hgf_status st = enter(ctx);
+  if (st != HGF_OK) return st;
+  if (!img) return set_err(ctx, HGF_EINVAL, "img is NULL");
+  st = check_outputs(ctx, g, cost, cost_dtype, L, filtered, filtered_dtype, labels, best);
+  if (st != HGF_OK) return st;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  return filter_locked(ctx, g, img, cost, cost_dtype, L, filtered, labels, best,
+                       (cudaStream_t)stream);
+}
+
 hgf_status hgf_aggregate_margin(hgf_ctx *ctx, const hgf_guidance *g, const void *cost,
                                 int cost_dtype, int L, int32_t *labels, float *best,
                                 float *margin, void *stream) {
@@ -616,12 +645,8 @@ hgf_status hgf_filter_host(hgf_ctx *ctx, const float *img, int C, int H, int W,
     if (st != HGF_OK) return st;
     ctx->host_guidance = g;
   }
-  st = prepare_locked(ctx, ctx->host_guidance, img_d, s);
-  if (st != HGF_OK) return st;
-  e = cudaStreamWaitEvent(s, ctx->io_done, 0);
-  if (e != cudaSuccess) return cuda_fail_locked(ctx, e, "hgf_filter_host upload wait");
-  st = aggregate_locked(ctx, ctx->host_guidance, cost_d, cost_dtype, L, nullptr,
-                        labels ? labels_d : nullptr, best ? best_d : nullptr, s);
+  st = filter_locked(ctx, ctx->host_guidance, img_d, cost_d, cost_dtype, L, nullptr,
+                     labels ? labels_d : nullptr, best ? best_d : nullptr, s, ctx->io_done);
   if (st != HGF_OK) return st;
   if (labels) e = cudaMemcpyAsync(labels, labels_d, HW * 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && best) e = cudaMemcpyAsync(best, best_d, HW * 4, cudaMemcpyDeviceToHost, s);

@@ -340,6 +340,9 @@ cudaError_t launch_onepass(const hgf_guidance *g, const void *cost, int cost_dty
                            Profiler *prof);
 constexpr int kFusedLabels = 2;     // labels per work item of the single-pass kernel
 constexpr int kFusedCtasPerSm = 3;  // resident CTAs per SM its persistent grid is sized for
+// ... for n guidance channels: up to n = 3 its state fits 128 registers a thread and four CTAs
+// share an SM; larger n take 168 registers, three CTAs
+__host__ __device__ constexpr int fused_ctas_per_sm(int n) { return n <= 3 ? 4 : kFusedCtasPerSm; }
 // Shared memory of the single-pass kernel, whether the plan may select it for g, and the bytes
 // of its ring buffer for a persistent grid of `ctas` CTAs.
 size_t onepass_smem(int n, int r);

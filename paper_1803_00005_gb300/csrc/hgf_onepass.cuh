@@ -462,7 +462,7 @@ __device__ __forceinline__ void fused_item(const FusedJob &jb, const CUtensorMap
 }
 
 template <int B, int K, typename CT, bool COMP>
-__global__ void __launch_bounds__(NT, kFusedCtasPerSm)
+__global__ void __launch_bounds__(NT, fused_ctas_per_sm(basis_n(B)))
     k_fused(const __grid_constant__ FusedJob jb, const __grid_constant__ CUtensorMap rec_map,
             float *__restrict__ ring_ws, size_t ring_stride, int *status) {
   constexpr int C1 = basis_n(B) + 1, REC = record_floats(basis_n(B));

@@ -40,7 +40,7 @@ EXPORTED = [
     "hgf_batch_create", "hgf_batch_run", "hgf_batch_launch_graph", "hgf_batch_destroy",
     "hgf_device_status", "hgf_batched_inverse", "hgf_cost_volume", "hgf_aggregate_stereo",
     "hgf_refine_lr", "hgf_autotune", "hgf_watchdog_probe", "hgf_stereo_host",
-    "hgf_aggregate_margin", "hgf_wta_margin",
+    "hgf_aggregate_margin", "hgf_wta_margin", "hgf_filter",
 ]
 
 
@@ -130,6 +130,7 @@ def lib():
                                       P(c_double)]),
         "hgf_guidance_export": (c_int, [vp, vp, vp, vp, vp]),
         "hgf_aggregate": (c_int, [vp, vp, vp, c_int, c_int, vp, c_int, vp, vp, vp]),
+        "hgf_filter": (c_int, [vp, vp, vp, vp, c_int, c_int, vp, c_int, vp, vp, vp]),
         "hgf_aggregate_plain": (c_int, [vp, vp, vp, c_int, c_int, vp, c_int, vp, vp, vp]),
         "hgf_aggregate_static": (c_int, [vp, vp, vp, c_int, c_int, vp, c_int, vp, vp, vp]),
         "hgf_serve_create": (c_int, [c_int, ctypes.c_size_t, c_int, c_int, c_int, c_int, P(vp)]),
@@ -283,6 +284,17 @@ def hgf_aggregate(ctx, g, cost, filtered=None, labels=None, best=None, stream=No
     L = cost.shape[0]
     _check(ctx, lib().hgf_aggregate(ctx, g, _ptr(cost), _dtype_code(cost), L, _ptr(filtered),
                                     HGF_F32, _ptr(labels), _ptr(best), _stream(stream)))
+
+
+def hgf_filter(ctx, g, img, cost, filtered=None, labels=None, best=None, stream=None):
+    """hgf_guidance_update(g, img) + hgf_aggregate(g, cost) in one call (see include/hgf.h)."""
+    for t, nm in ((img, "img"), (cost, "cost"), (filtered, "filtered"), (labels, "labels"),
+                  (best, "best")):
+        _require_cuda(t, nm)
+    L = cost.shape[0]
+    _check(ctx, lib().hgf_filter(ctx, g, _ptr(img), _ptr(cost), _dtype_code(cost), L,
+                                 _ptr(filtered), HGF_F32, _ptr(labels), _ptr(best),
+                                 _stream(stream)))
 
 
 def hgf_aggregate_static(ctx, g, cost, filtered=None, labels=None, best=None, stream=None):
