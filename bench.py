@@ -498,8 +498,8 @@ def run_oracle(w, crop, reps):
 
 # The oracle's measured rate on the GPU machine's host (one core, 450x375 / L = 60 / n = 9), used only to
 # size the reference arm's sample so that its run stays within a few minutes.
-ORACLE_MPLS_ESTIMATE = 1.8
-REFERENCE_BUDGET_S = 210.0
+ORACLE_MPLS_ESTIMATE = 1.05
+REFERENCE_BUDGET_S = 150.0
 
 
 def reference_crop(w, steps_total):

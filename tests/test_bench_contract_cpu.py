@@ -80,15 +80,17 @@ def test_clock_sampler_parses_rows_and_reasons():
 
 
 def test_reference_sample_and_fp32_peak():
-    """The reference arm times the whole workload when its steps fit the time budget (the
-    driver's 20 + 5 steps on the 450x375 / 60-label workload) and a proportional centred crop
-    otherwise; the FP32 peak follows the SM count and clock it is given."""
+    """The reference arm times the whole workload when its steps fit the time budget (10 steps
+    of the 450x375 / 60-label workload) and a proportional centred crop otherwise (the 20 + 5
+    steps of a default driver run, and 305); the FP32 peak follows the SM count and clock it is
+    given."""
     sys.path.insert(0, ROOT)
     import bench
     w = bench.WORKLOADS["quarter"]
-    assert bench.reference_crop(w, 25) == (450, 375)
-    cw, ch = bench.reference_crop(w, 305)
-    assert cw < 450 and ch < 375 and abs(cw / ch - 450 / 375) < 0.05
-    assert cw * ch * 60 * 305 <= bench.REFERENCE_BUDGET_S * bench.ORACLE_MPLS_ESTIMATE * 1e6
+    assert bench.reference_crop(w, 10) == (450, 375)
+    for steps in (25, 305):
+        cw, ch = bench.reference_crop(w, steps)
+        assert cw < 450 and ch < 375 and abs(cw / ch - 450 / 375) < 0.05
+        assert cw * ch * 60 * steps <= bench.REFERENCE_BUDGET_S * bench.ORACLE_MPLS_ESTIMATE * 1e6
     assert abs(bench.fp32_peak_tflops(152, 2070.0) - 152 * 128 * 2 * 2.07e9 / 1e12) < 1e-9
     assert abs(bench.fp32_peak_tflops(148, 1800.0) - 148 * 128 * 2 * 1.8e9 / 1e12) < 1e-9
