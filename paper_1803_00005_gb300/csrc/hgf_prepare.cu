@@ -2,7 +2,8 @@
 // box sums), covariance assembly (Sec. 5.1) and the per-pixel inverse by the Sherman-Morrison
 // recursion of Prop. 1 (Sec. 3). Runs once per guidance; the result stays resident.
 //
-// Numerics: every guidance channel is shifted by its image mean c_i before moments are formed.
+// Numerics: every guidance channel is shifted by c_i, its mean over a fixed sample of pixels
+// (k_shifted_guidance), before moments are formed.
 // The centred form is exactly invariant to G_i -> G_i - c_i (Sigma, cov and q do not change), and
 // the shift shrinks the cancellation in A(G_i G_j) - mu_i mu_j. Window sums are float32 direct
 // sums of 2r+1 terms per axis; the assembly Sigma = A(GG^T) - mu mu^T and the recursion run in the
@@ -73,27 +74,34 @@ cudaError_t launch_make_guidance(const float *img, int C, int H, int W, const Ba
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- per-channel mean (deterministic)
-constexpr int kMeanBlocks = 160;
-constexpr int kMeanThreads = 256;
+// ------------------------------------------------------ shifted guidance (deterministic shift)
+// The shift c_i only conditions the float32 moment sums (the centred form is exactly invariant to
+// G_i -> G_i - c_i, and the paper form undoes it exactly in float64), so any value near the
+// image mean of G_i serves: c_i is the mean of G_i over a fixed sample of kShiftSamples pixels
+// spread evenly over the image. Every CTA computes it from the same pixels in the same order (a
+// fixed per-thread partial, then a fixed tree over the CTA), so all CTAs get identical values,
+// and CTA 0 stores them in `shift`. Then G_i - c_i for the CTA's pixels.
+constexpr int kShiftSamples = 1024;
+constexpr int kShiftThreads = 256;
 
-// partial[b * n + i] = sum of G_i over block b's fixed pixel range (float64, fixed order), with
-// G_i evaluated from the input image.
 template <int B>
-__global__ void __launch_bounds__(kMeanThreads) k_mean_partial(const float *__restrict__ img,
-                                                               int HW,
-                                                               double *__restrict__ partial) {
-  // the shift only conditions the float32 sums (the centred form is exactly invariant to it), so
-  // float32 sums of a few pixels per thread are plenty; the block totals are kept in float64
+__global__ void __launch_bounds__(kShiftThreads) k_shifted_guidance(const float *__restrict__ img,
+                                                                    int HW,
+                                                                    float *__restrict__ shift,
+                                                                    float *__restrict__ G) {
   constexpr int N = basis_n(B), C = basis_channels_in(B);
-  __shared__ float red[kMeanThreads / 32][N];
+  constexpr int NW = kShiftThreads / 32;
+  __shared__ float red[NW][N];
+  __shared__ float sh_s[N];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const float zero[N] = {};
   float acc[N];
 #pragma unroll
   for (int i = 0; i < N; ++i) acc[i] = 0.f;
-  const int per = (HW + gridDim.x - 1) / gridDim.x;
-  const int p0 = blockIdx.x * per, p1 = min(HW, p0 + per);
-  for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+  const int ns = min(kShiftSamples, HW);
+#pragma unroll 4
+  for (int k = t; k < ns; k += kShiftThreads) {  // the loads of all four samples in flight
+    const int p = (int)(((long long)k * HW) / ns);
     float x[C], g[N];
 #pragma unroll
     for (int c = 0; c < C; ++c) x[c] = __ldg(img + (size_t)c * HW + p);
@@ -101,7 +109,6 @@ __global__ void __launch_bounds__(kMeanThreads) k_mean_partial(const float *__re
 #pragma unroll
     for (int i = 0; i < N; ++i) acc[i] += g[i];
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     float v = acc[i];
@@ -110,46 +117,23 @@ __global__ void __launch_bounds__(kMeanThreads) k_mean_partial(const float *__re
     if (lane == 0) red[warp][i] = v;
   }
   __syncthreads();
-  if (threadIdx.x < N) {
-    double s = 0.0;
-    for (int w = 0; w < kMeanThreads / 32; ++w) s += (double)red[w][threadIdx.x];
-    partial[blockIdx.x * N + threadIdx.x] = s;
-  }
-}
-
-// Shifted guidance planes G_i - c_i (used by the moment sums and the plain form). Every CTA
-// first reduces the per-block partial sums to the image means c_i itself (one warp per channel,
-// a fixed order, so all CTAs get identical values); CTA 0 also stores them in `shift`.
-template <int B>
-__global__ void __launch_bounds__(256) k_shifted_guidance(const float *__restrict__ img,
-                                                          const double *__restrict__ partial,
-                                                          int nblk, int HW,
-                                                          float *__restrict__ shift,
-                                                          float *__restrict__ G) {
-  constexpr int N = basis_n(B), C = basis_channels_in(B);
-  __shared__ float sh_s[N];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  for (int i = warp; i < N; i += nwarp) {
-    double s = 0.0;
-    for (int b = lane; b < nblk; b += 32) s += partial[b * N + i];
+  if (t < N) {
+    float v = 0.f;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-    if (lane == 0) {
-      const float c = (float)(s / HW);
-      sh_s[i] = c;
-      if (blockIdx.x == 0) shift[i] = c;
-    }
+    for (int w = 0; w < NW; ++w) v += red[w][t];
+    const float c = v / (float)ns;
+    sh_s[t] = c;
+    if (blockIdx.x == 0) shift[t] = c;
   }
   __syncthreads();
   float sh[N];
 #pragma unroll
   for (int i = 0; i < N; ++i) sh[i] = sh_s[i];
-  // grid-stride over pixels: a few pixels per thread, so that fewer CTAs repeat the reduction
-  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < (size_t)HW;
-       p += (size_t)gridDim.x * blockDim.x) {
+  const int p = blockIdx.x * kShiftThreads + t;
+  if (p < HW) {
     float x[C], g[N];
 #pragma unroll
-    for (int c = 0; c < C; ++c) x[c] = img[(size_t)c * HW + p];
+    for (int c = 0; c < C; ++c) x[c] = __ldg(img + (size_t)c * HW + p);
     eval_basis<B>(x, sh, g);
 #pragma unroll
     for (int i = 0; i < N; ++i) G[(size_t)i * HW + p] = g[i];
@@ -590,8 +574,7 @@ static bool launch_inverse_n(const float *mom, const hgf_guidance *g, cudaStream
 size_t prepare_workspace_bytes(int n, int H, int W) {
   size_t M = (size_t)n + (size_t)n * (n + 1) / 2;
   size_t plane = ((M * (size_t)H * W * sizeof(float) + 255) / 256) * 256;
-  size_t part = (size_t)kMeanBlocks * n * sizeof(double);
-  return 2 * plane + part;  // row sums, window sums, mean partials
+  return 2 * plane;  // row sums, window sums
 }
 
 cudaError_t launch_prepare(hgf_guidance *g, const float *img, void *ws, size_t ws_size,
@@ -604,22 +587,15 @@ cudaError_t launch_prepare(hgf_guidance *g, const float *img, void *ws, size_t w
   const size_t plane = ((M * HW * sizeof(float) + 255) / 256) * 256;
   float *rows = (float *)ws;
   float *mom = (float *)((char *)ws + plane);
-  double *partial = (double *)((char *)ws + 2 * plane);
 
   cudaError_t e = cudaMemcpyAsync(g->img, img, (size_t)g->C * HW * sizeof(float),
                                   cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return e;
   dispatch_basis(b, [&](auto bc) {
     constexpr int B = decltype(bc)::value;
-    {
-      LaunchScope ls(prof, "k_mean_partial", s);
-      k_mean_partial<B><<<kMeanBlocks, kMeanThreads, 0, s>>>(g->img, HW, partial);
-    }
-    {
-      LaunchScope ls(prof, "k_shifted_guidance", s);
-      k_shifted_guidance<B><<<(HW + 1023) / 1024, 256, 0, s>>>(g->img, partial, kMeanBlocks, HW,
-                                                               g->shift, g->G);
-    }
+    LaunchScope ls(prof, "k_shifted_guidance", s);
+    k_shifted_guidance<B><<<(HW + kShiftThreads - 1) / kShiftThreads, kShiftThreads, 0, s>>>(
+        g->img, HW, g->shift, g->G);
   });
   if (n <= 9 && 2 * g->r + 1 < kStripThreads) {
     int dev = 0, sms = 1;
