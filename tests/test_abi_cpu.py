@@ -58,3 +58,4 @@ def test_null_context_rejected(lib):
     from paper_1803_00005_gb300 import hgf
     assert lib.hgf_aggregate(None, None, None, 0, 1, None, 0, None, None, None) == hgf.HGF_EINVAL
     assert lib.hgf_prepare(None, None, 3, 4, 4, None, None, None) == hgf.HGF_EINVAL
+    assert lib.hgf_filter(None, None, None, None, 0, 1, None, 0, None, None, None) == hgf.HGF_EINVAL
