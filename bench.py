@@ -119,8 +119,9 @@ def parse():
                     help="skip the warm, plain-form, single-pass and served legs of the line")
     ap.add_argument("--serve-rate", type=float, default=20.0,
                     help="requests per second of the default line's short served leg")
-    ap.add_argument("--cpu-crop", type=int, nargs=2, default=(225, 188),
-                    help="width height of the centred crop the CPU baseline runs on")
+    ap.add_argument("--cpu-crop", type=int, nargs=2, default=None,
+                    help="width height of the centred crop the CPU baseline runs on (default: "
+                         "the largest whose two repetitions take about 15 s)")
     ap.add_argument("--serve", action="store_true",
                     help="open-loop serving run (Poisson arrivals) instead of the step benchmark")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean requests per second")
@@ -503,6 +504,23 @@ ORACLE_MPLS_ESTIMATE = 1.05
 REFERENCE_BUDGET_S = 150.0
 
 
+CPU_SAMPLE_S = 15.0  # target CPU time of the default line's cpu_baseline (two repetitions)
+
+
+def cpu_sample_crop(w):
+    """The whole workload, or the largest centred crop (same aspect), whose two oracle repetitions
+    take about CPU_SAMPLE_S at the oracle's measured rate, scaled from n = 9 by the flops per
+    px*label (2n^2 + 17n + 10) of the workload's degree."""
+    n = {1: 3, 2: 9, 3: 19}.get(w["degree"], 9)
+    rate = ORACLE_MPLS_ESTIMATE * 325.0 / (2 * n * n + 17 * n + 10)
+    full = w["width"] * w["height"] * w["n_labels"]
+    fit = CPU_SAMPLE_S * rate * 1e6 / 2
+    if full <= fit:
+        return (w["width"], w["height"])
+    s = (fit / full) ** 0.5
+    return (max(8, int(w["width"] * s)), max(8, int(w["height"] * s)))
+
+
 def reference_crop(w, steps_total):
     """The whole image when (warm-up + timed) oracle steps on it fit the time budget at the
     estimated rate, else the largest centred crop (same aspect) that does."""
@@ -626,20 +644,23 @@ def main():
 
     cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        crop = (min(args.cpu_crop[0], w["width"]), min(args.cpu_crop[1], w["height"]))
+        crop = ((min(args.cpu_crop[0], w["width"]), min(args.cpu_crop[1], w["height"]))
+                if args.cpu_crop else cpu_sample_crop(w))
         res = run_oracle(w, crop, 2)            # before any GPU work in this process
         tot = sum(res["times"])
         cpu = dict(value=res["units"] * len(res["times"]) / tot / 1e6, unit=UNIT, cores=1,
                    kind="oracle",
-                   sample=f"centred {crop[0]}x{crop[1]} crop, all {w['n_labels']} labels, "
-                          f"prepare + aggregate + WTA, 2 repetitions ({tot:.1f} s), float64 numpy, "
-                          f"one thread")
+                   sample=(f"the whole {w['width']}x{w['height']} workload"
+                           if crop == (w["width"], w["height"]) else
+                           f"centred {crop[0]}x{crop[1]} crop") +
+                          f", all {w['n_labels']} labels, prepare + aggregate + WTA, 2 repetitions "
+                          f"({tot:.1f} s), float64 numpy, one thread")
         try:
             resp = run_oracle_pool(w, crop, 2)
             tp = sum(resp["times"])
             cpu_all = dict(value=resp["units"] * len(resp["times"]) / tp / 1e6, unit=UNIT,
                            cores=resp["cores"], kind="oracle",
-                           sample=f"same crop, labels split over {resp['cores']} spawned "
+                           sample=f"same sample, labels split over {resp['cores']} spawned "
                                   f"processes (one thread each), 2 repetitions ({tp:.1f} s)")
         except (RuntimeError, subprocess.TimeoutExpired, OSError) as exc:
             cpu_all = dict(value=None, error=str(exc)[-300:])

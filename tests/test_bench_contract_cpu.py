@@ -92,5 +92,11 @@ def test_reference_sample_and_fp32_peak():
         cw, ch = bench.reference_crop(w, steps)
         assert cw < 450 and ch < 375 and abs(cw / ch - 450 / 375) < 0.05
         assert cw * ch * 60 * steps <= bench.REFERENCE_BUDGET_S * bench.ORACLE_MPLS_ESTIMATE * 1e6
+    # the default line's CPU baseline: about CPU_SAMPLE_S of oracle work in two repetitions
+    cw, ch = bench.cpu_sample_crop(w)
+    assert cw <= 450 and ch <= 375
+    t = 2 * cw * ch * 60 / (bench.ORACLE_MPLS_ESTIMATE * 1e6)
+    assert 0.8 * bench.CPU_SAMPLE_S <= t <= bench.CPU_SAMPLE_S
+    assert bench.cpu_sample_crop(bench.WORKLOADS["small"]) == (64, 48)
     assert abs(bench.fp32_peak_tflops(152, 2070.0) - 152 * 128 * 2 * 2.07e9 / 1e12) < 1e-9
     assert abs(bench.fp32_peak_tflops(148, 1800.0) - 148 * 128 * 2 * 1.8e9 / 1e12) < 1e-9
