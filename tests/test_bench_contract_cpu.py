@@ -82,7 +82,7 @@ def test_clock_sampler_parses_rows_and_reasons():
 def test_reference_sample_and_fp32_peak():
     """The reference arm times the whole workload when its steps fit the time budget (10 steps
     of the 450x375 / 60-label workload) and a proportional centred crop otherwise (the 20 + 5
-    steps of a default driver run, and 305); the FP32 peak follows the SM count and clock it is
+    steps of a typical short run, and 305); the FP32 peak follows the SM count and clock it is
     given."""
     sys.path.insert(0, ROOT)
     import bench
