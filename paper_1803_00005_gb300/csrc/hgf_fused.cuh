@@ -442,10 +442,14 @@ constexpr size_t apply_smem_bytes(int r) {
 
 // One label per CTA. RING: the outgoing coefficient row comes from the thread's shared-memory
 // ring; otherwise it is reloaded from device memory (used when the ring does not fit).
-// no minimum CTA count: capping registers for 5, 6 or 8 CTAs per SM made k_apply slower
-// (450x375, n = 9: 0.29 ms -> 0.41-0.44 ms)
+// No minimum CTA count for n <= 9: capping registers for 5, 6 or 8 CTAs per SM made k_apply
+// slower (450x375, n = 9: 0.29 ms -> 0.41-0.44 ms). At n = 19 a cap for three CTAs per SM (221 ->
+// 168 registers, a few spills) made it faster (1280x960, L = 128: 8.38 -> 7.90 ms).
+template <int B>
+__host__ __device__ constexpr int apply_min_blocks() { return basis_n(B) > 9 ? 3 : 1; }
+
 template <int B, bool RING, bool COMP>
-__global__ void __launch_bounds__(NT) k_apply(const float *__restrict__ coef, int H, int W, int r,
+__global__ void __launch_bounds__(NT, apply_min_blocks<B>()) k_apply(const float *__restrict__ coef, int H, int W, int r,
                                               const float *__restrict__ img,
                                               const float *__restrict__ shift,
                                               unsigned long long *__restrict__ keys,
